@@ -1,0 +1,336 @@
+"""Throughput of the facet-to-IQ echo path on B300.
+
+One step = one harm_echo_accumulate call over the whole workload: every facet of
+the 4 km x 2 km wave scene (2000 x 1000 facets of 2 m), every pulse of the burst
+(2048 at 1700 Hz) and every receive channel (Harmony A and B x 3 phase centres),
+i.e. 2.4576e10 facet-pulse-channel contributions, spread by the 8-tap
+Kaiser-sinc into 6 x 2048 x 4096 complex64 IQ samples.
+
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import harm_scenes as hs  # noqa: E402
+
+METRIC = "facet·pulse·channel contributions/s at stated IQ error vs FP64 oracle; adjoint/fwd ratio"
+UNIT = "contributions/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--pulses", type=int, default=2048, help="burst length of the scene")
+    ap.add_argument("--window", type=int, default=0,
+                    help="pulses per step (0 = the whole burst); for the slow FP64 form")
+    ap.add_argument("--cpu-pulses", type=int, default=1, help="pulses in the oracle sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_flops_per_contribution(nc, nb=32, nw=256, orders=5):
+    """FP32 flop count per contribution of the mixed path (FMA = 2 flops), from the
+    arithmetic the formulation needs; per-facet-pulse terms shared by the nc
+    channels and the per-batch time-Taylor contraction are amortised."""
+    per_channel = 2 * 118          # Rx leg, NRCS, amplitude, phase, range position, taps scale
+    taps = 2 * 8 * 10              # 8 degree-10 tap polynomials
+    per_facet_pulse = 2 * 3 * (orders - 1) + 2 * 38   # Horner + Tx leg
+    generator = 2 * nw * (2 + 3 * orders * 2) / nb     # Taylor coefficients per facet, per pulse
+    return per_channel + taps + (per_facet_pulse + generator) / nc
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except OSError:
+        return None
+
+
+def run_oracle_sample(desc, n_pulses_sample):
+    import oracle
+    pulses = [int(round(v)) for v in np.linspace(0, desc["n_pulses"] - 1, n_pulses_sample)]
+    t0 = time.perf_counter()
+    iq = oracle.echo(desc, pulses)
+    dt = time.perf_counter() - t0
+    units = hs.n_facets(desc) * len(pulses) * len(desc["rx"])
+    return {"pulses": pulses, "iq": iq, "seconds": dt, "units": units, "cores": oracle.num_threads()}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    desc = hs.ati_scene(n_pulses=args.pulses)
+    samples = []
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps are not repeated
+    for _ in range(args.steps):
+        samples.append(run_oracle_sample(desc, args.cpu_pulses))
+    secs = sum(s["seconds"] for s in samples)
+    units = sum(s["units"] for s in samples)
+    value = units / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "ati_4x2km_2048p_6ch", "facets": hs.n_facets(desc),
+                   "pulses": desc["n_pulses"], "channels": len(desc["rx"]), "range_samples": desc["n_range"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": samples[0]["cores"], "kind": "oracle",
+                         "sample": "%d pulse(s) x all %d facets x %d channels per step" % (
+                             args.cpu_pulses, hs.n_facets(desc), len(desc["rx"]))},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    from paper_2405_09938_b300 import harm
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    prec = harm.HARM_PREC_MIXED if args.precision == "mixed" else harm.HARM_PREC_FP64
+    cdt = torch.complex64 if prec == harm.HARM_PREC_MIXED else torch.complex128
+    desc = hs.ati_scene(n_pulses=args.pulses)
+    nc, nr = len(desc["rx"]), desc["n_range"]
+    np_step = desc["n_pulses"] if args.window <= 0 else min(args.window, desc["n_pulses"])
+    n0_step = (desc["n_pulses"] - np_step) // 2
+    units = hs.n_facets(desc) * np_step * nc
+
+    stream = torch.cuda.current_stream()
+    scene = harm.harm_scene_create(desc, prec, stream)
+    iq = torch.empty((nc, np_step, nr), dtype=cdt, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step(zero=True):
+        harm.harm_echo_accumulate(scene, n0_step, np_step, iq, zero_first=zero)
+
+    for _ in range(args.warmup):
+        step()
+    harm.harm_scene_sync(scene)
+
+    # -- timed region: K steps, device time by CUDA events, L2 flushed between steps
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    harm.harm_scene_sync(scene)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    t_max = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    value = world * units * args.steps / (total_ms * 1e-3)
+
+    # -- roofline of the accumulator kernel alone (no memset), same stream
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(max(1, args.steps))]
+    for a, b in kev:
+        flush.zero_()
+        a.record(stream)
+        step(zero=False)
+        b.record(stream)
+    torch.cuda.synchronize()
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
+
+    # -- end to end through the public API with host buffers: scene creation
+    # (host precompute + table upload), accumulate, IQ copied to pinned host memory
+    host_iq = torch.empty((nc, np_step, nr), dtype=cdt, pin_memory=True)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2d = 0
+    for _ in range(e2e_steps):
+        sc = harm.harm_scene_create(desc, prec, stream)
+        h2d = _scene_table_bytes(desc, prec)
+        harm.harm_echo_accumulate(sc, n0_step, np_step, iq, zero_first=True)
+        host_iq.copy_(iq, non_blocking=True)
+        torch.cuda.synchronize()
+        sc.close()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    d2h = iq.numel() * iq.element_size()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    flops = algorithmic_flops_per_contribution(nc) * units
+    peaks = measured_peaks()
+    sm_max = (peaks or {}).get("sm_max_mhz", 2032.0)
+    fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, unit counts x max SM clock
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if prec == harm.HARM_PREC_MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": "ati_4x2km_2048p_6ch", "facets": hs.n_facets(desc), "pulses": np_step,
+                   "channels": nc, "range_samples": nr, "precision": args.precision,
+                   "output": "complex64" if cdt == torch.complex64 else "complex128",
+                   "l2": "flushed between steps (256 MiB write); IQ output %.0f MB" % (d2h / 1e6),
+                   "replicas": world},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "kernel": "accumulate_mixed_kernel" if prec == harm.HARM_PREC_MIXED else "accumulate_f64_kernel",
+                     "kernel_ms": kern_ms, "flops_per_contribution": flops / units,
+                     "peak_basis": "148 SM x 128 FP32 lanes x 2 x %.0f MHz (max SM clock)" % sm_max},
+        "clocks": clk,
+        "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "what": "harm_scene_create + harm_echo_accumulate + IQ to pinned host memory"},
+        "gpu_launches": args.steps * _launches_per_step(desc, prec, np_step),
+    }
+    if not args.no_cpu:
+        cpu = run_oracle_sample(desc, args.cpu_pulses)
+        # IQ error of the GPU path on the sampled pulses
+        sel = [p - n0_step for p in cpu["pulses"] if n0_step <= p < n0_step + np_step]
+        if sel:
+            got = iq.cpu().numpy()[:, sel, :]
+            want = cpu["iq"][:, [i for i, p in enumerate(cpu["pulses"]) if n0_step <= p < n0_step + np_step], :]
+            err = float(np.sqrt(np.sum(np.abs(got - want) ** 2) / np.sum(np.abs(want) ** 2)))
+            line["iq_rel_rms"] = err
+            line["iq_error_sample"] = "pulses %s, all channels and range samples" % sel
+        line["cpu_baseline"] = {"value": cpu["units"] / cpu["seconds"], "unit": UNIT, "cores": cpu["cores"],
+                                "kind": "oracle",
+                                "sample": "%d pulse(s) of the workload x %d facets x %d channels (%.1f s)" % (
+                                    len(cpu["pulses"]), hs.n_facets(desc), nc, cpu["seconds"])}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _launches_per_step(desc, prec, np_step):
+    from paper_2405_09938_b300 import harm
+    if prec == harm.HARM_PREC_MIXED:
+        batches = math.ceil(np_step / 32) + 1
+        return max(1, math.ceil(batches / 65535))
+    return max(1, math.ceil(np_step / 65535))
+
+
+def _scene_table_bytes(desc, prec):
+    from paper_2405_09938_b300 import harm
+    nw = desc["n_omega"] * desc["n_theta"]
+    npul, nc, nx, ny = desc["n_pulses"], len(desc["rx"]), desc["nx"], desc["ny"]
+    pulse = npul * (8 * 2 + 8 * 10) + npul * nc * (8 * 10 + 16)
+    if prec == harm.HARM_PREC_MIXED:
+        waves = nw * (nx + ny) * 8 + math.ceil(npul / 32) * nw * 15 * 8 + npul * 4 + nw * 24
+    else:
+        waves = nw * (nx + ny + npul) * 16 + nw * 24
+    return pulse + waves + 16
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * harm.h -- C ABI of the B300-native facet-to-IQ echo generator.
+ *
+ * The library computes the raw-data hot path of a bistatic SAR/ATI scene-and-
+ * instrument simulator (HEEPS/MARE, Sec. II-B and Sec. IV of the paper): for
+ * every pulse and receive channel, sea-surface facets are advanced to the pulse
+ * time, their complex amplitudes (Eq. 3, Eq. 16) are weighted by the transmit
+ * and receive antenna patterns, carry the two-way phase
+ * exp(-i K0 (r_t + r_r + v_c t)) with v_c from Eq. 4, and are summed into range
+ * samples (Eq. 17, here with a short Kaiser-windowed sinc in place of the box).
+ *
+ * Conventions shared by every entry point:
+ *   - Frame: flat-earth local frame, x along-track, y ground range away from the
+ *     radars, z up, origin at the scene centre on the mean surface [m].
+ *   - Device memory passed in (iq, state, residual, gradients) belongs to the
+ *     caller and must be device memory of the current CUDA device. The scene owns
+ *     only its own tables; nothing is allocated per call.
+ *   - Every call is asynchronous on the scene's CUDA stream. A returned status
+ *     reports launch-time errors; device-side errors are reported by the next
+ *     call or by harm_scene_sync().
+ *   - No C++ exception crosses this boundary. On any non-OK status,
+ *     harm_last_error() returns a thread-local message.
+ *   - A scene may be used by one host thread at a time.
+ *
+ * Complex outputs are interleaved (re, im) in the element type given by
+ * harm_dtype; IQ layout is [n_channels][np][n_range], range fastest.
+ */
+#ifndef HARM_H
+#define HARM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HARM_ABI_VERSION 1u
+#define HARM_MAX_CHANNELS 16
+
+typedef enum {
+    HARM_OK = 0,
+    HARM_E_INVALID = 1,     /* bad argument or descriptor */
+    HARM_E_CUDA = 2,        /* CUDA runtime error (message has the CUDA text) */
+    HARM_E_OOM = 3,         /* device or host allocation failed */
+    HARM_E_TIMEOUT = 4,     /* a bounded device wait gave up */
+    HARM_E_UNSUPPORTED = 5  /* valid request this build does not implement */
+} harm_status;
+
+typedef enum {
+    HARM_C64 = 0,  /* complex64: float re, float im */
+    HARM_C128 = 1  /* complex128: double re, double im */
+} harm_dtype;
+
+typedef enum {
+    HARM_PREC_FP64 = 0,  /* every step in double precision */
+    HARM_PREC_MIXED = 1  /* FP64 only for per-pulse state, reference ranges and
+                            per-tile range offsets; FP32 for the rest */
+} harm_precision;
+
+/* One antenna phase centre moving linearly: P(t) = pos0 + vel * t, t = 0 at the
+   first pulse of the burst. len_az / len_el are the aperture lengths used by the
+   sinc^2 pattern (Sec. III-B, Eq. 16). */
+typedef struct {
+    double pos0[3];
+    double vel[3];
+    double len_az;
+    double len_el;
+} harm_antenna;
+
+/* Scene, instrument and acquisition descriptor (the inputs of Sec. II-B: instrument,
+   geometry, acquisition mode and geophysical scene). All fields are copied by
+   harm_scene_create; the rx array may be freed afterwards. */
+typedef struct {
+    uint32_t abi_version;   /* HARM_ABI_VERSION */
+    uint32_t struct_size;   /* sizeof(harm_scene_desc) */
+    double f0_hz;           /* carrier frequency */
+    double fs_hz;           /* range sampling rate; bin = c / fs of bistatic path */
+    double prf_hz;          /* pulse repetition frequency; t_n = n / prf */
+    int32_t n_pulses;       /* pulses in the burst */
+    int32_t n_range;        /* range samples per pulse and channel */
+    harm_antenna tx;        /* transmitter */
+    int32_t n_channels;     /* receive channels, 1 .. HARM_MAX_CHANNELS */
+    const harm_antenna *rx; /* [n_channels] receive phase centres (host memory) */
+    int32_t nx, ny;         /* facet grid; facet id f = iy * nx + ix */
+    double facet_m;         /* facet edge; centre x = (ix + 1/2 - nx/2) facet_m */
+    int32_t n_omega;        /* wave grid: frequency bins (0 = no waves) */
+    int32_t n_theta;        /* wave grid: directions */
+    double u10;             /* wind speed [m/s] (JONSWAP fetch laws) */
+    double fetch_m;         /* fetch [m] */
+    double wind_dir_rad;    /* direction the wind blows toward, from +x */
+    double spread_s;        /* cos^2s spreading exponent s */
+    double gamma;           /* JONSWAP peak enhancement */
+    uint64_t wave_seed;     /* Philox key of the wave phases */
+    double current_u;       /* uniform surface current [m/s] (Eq. 4) */
+    double current_v;
+    double sigma0_base;     /* NRCS base value */
+    double wind_mod;        /* NRCS wind modulation m in (1 + m cos phi_wind) */
+    int32_t epoch_pulses;   /* pulses per speckle coherence epoch (0 = one epoch) */
+    uint64_t speckle_seed;  /* Philox key of the speckle */
+    int32_t static_surface; /* 1: heights 0 and NRCS = sigma0_base everywhere */
+    int32_t taps;           /* 1 (Eq. 17 box) or 8 (Kaiser-windowed sinc) */
+    double kaiser_beta;     /* Kaiser window beta for taps = 8 */
+    int32_t precision;      /* harm_precision */
+} harm_scene_desc;
+
+typedef struct harm_scene harm_scene; /* opaque, owned by the library */
+
+/* Scene sizes, filled by harm_scene_query. */
+typedef struct {
+    int64_t n_facets;
+    int32_t n_pulses, n_range, n_channels, n_waves;
+    int32_t precision;
+    int32_t pulse_batch;     /* pulses per work item of the accumulator */
+    double range_bin_m;      /* c / fs */
+    double range_start_m[HARM_MAX_CHANNELS]; /* R0 per channel */
+} harm_scene_info;
+
+/* Create a scene: validate the descriptor, build the wave component table
+   (linear surface, Sec. III), per-pulse platform state with light time (Eq. 3)
+   and range windows in FP64 on the host, and upload them to the current device on
+   `cuda_stream` (a cudaStream_t, NULL = default stream). *out receives the scene.
+   Errors: HARM_E_INVALID for a bad descriptor or NULL pointer, HARM_E_OOM,
+   HARM_E_CUDA. On error *out is set to NULL and nothing is leaked. */
+harm_status harm_scene_create(const harm_scene_desc *desc, void *cuda_stream, harm_scene **out);
+
+/* Release a scene and its device tables after its stream has drained. NULL is OK. */
+harm_status harm_scene_destroy(harm_scene *scene);
+
+/* Fill *info with the scene's sizes. */
+harm_status harm_scene_query(const harm_scene *scene, harm_scene_info *info);
+
+/* Per-cell NRCS base and current (u, v), on cells of cell_m starting at the
+   patch corner (cell index clamps at the edges). sigma0 [ncy*ncx] and uv
+   [ncy*ncx*2] are DEVICE pointers to doubles; either may be NULL to keep the
+   uniform value. The scene keeps the pointers: they must stay valid while the
+   scene is used. ncx = 0 removes the cell fields. */
+harm_status harm_scene_set_cells(harm_scene *scene, int32_t ncx, int32_t ncy, double cell_m,
+                                 const double *sigma0_dev, const double *uv_dev);
+
+/* Facet generator (Sec. III linear surface, Sec. IV-B "generate the surface"):
+   writes (eta, eta_x, eta_y) of every facet for pulses [n0, n0 + np) at the
+   bounce time of each pulse, to state_dev laid out [np][3][n_facets], in double
+   for HARM_PREC_FP64 scenes and in float for HARM_PREC_MIXED scenes.
+   Errors: HARM_E_INVALID for an out-of-range pulse window or NULL pointer. */
+harm_status harm_facets_generate(harm_scene *scene, int32_t n0, int32_t np, void *state_dev);
+
+/* Echo accumulator (Eq. 3, 4, 16, 17): adds the echo of every facet for pulses
+   [n0, n0 + np) and every channel into iq_dev, laid out [n_channels][np][n_range]
+   complex of `dtype`. zero_first = 1 clears iq_dev first (on the stream).
+   Sums use atomics: repeated runs agree to rounding, not bit for bit.
+   Errors: HARM_E_INVALID (window, pointer, dtype). */
+harm_status harm_echo_accumulate(harm_scene *scene, int32_t n0, int32_t np, void *iq_dev,
+                                 harm_dtype dtype, int32_t zero_first);
+
+/* Adjoint of harm_echo_accumulate with respect to the per-cell NRCS base and the
+   per-cell current (the transposed scatter as a gather over range bins): for the
+   misfit L = sum |IQ - target|^2 and residual r = IQ - target (resid_dev, same
+   layout and dtype as the IQ), adds dL/dsigma0_cell to grad_sigma0_dev [ncy*ncx]
+   and dL/d(u, v)_cell to grad_uv_dev [ncy*ncx*2] (device doubles, either may be
+   NULL). Requires cells set by harm_scene_set_cells. Facet states are recomputed,
+   not stored. Errors: HARM_E_INVALID, HARM_E_UNSUPPORTED. */
+harm_status harm_echo_adjoint(harm_scene *scene, int32_t n0, int32_t np, const void *resid_dev,
+                              harm_dtype dtype, double *grad_sigma0_dev, double *grad_uv_dev);
+
+/* Wait for the scene's stream and report device-side errors (bounded waits that
+   timed out, bounds flags) raised since the last check. */
+harm_status harm_scene_sync(harm_scene *scene);
+
+/* Thread-local text of the last non-OK status on this thread ("" if none). */
+const char *harm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HARM_H */

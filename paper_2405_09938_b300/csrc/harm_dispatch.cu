@@ -1,0 +1,151 @@
+// Launch dispatch by precision, and the host-side tables of the mixed path:
+// FP32 separable wave phasors, Taylor-in-time tables per pulse batch, and the
+// Kaiser-sinc tap polynomials.
+#include <cmath>
+#include <vector>
+
+#include "harm_internal.cuh"
+#include "harm_kernels.cuh"
+
+namespace harm {
+
+int mixed_batch_pulses();
+
+namespace {
+
+template <typename T>
+cudaError_t upload_raw(harm_scene *s, const std::vector<T> &h, const T **out)
+{
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, h.size() * sizeof(T));
+    if (e != cudaSuccess) return e;
+    s->allocs.push_back(p);
+    e = cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s->stream);
+    *out = (const T *)p;
+    return e;
+}
+
+// Kaiser-windowed sinc h(x) for the 8-tap kernel (half-width 4), with the window
+// from the scene's power-series coefficients.
+double kaiser_sinc_host(const DevScene &S, double x)
+{
+    double q = 0.25 * x;
+    double v = 1.0 - q * q;
+    if (v <= 0.0) return 0.0;
+    double w = 0.0;
+    for (int k = S.n_i0 - 1; k >= 0; --k) w = w * v + S.i0c[k];
+    double sc = (x == 0.0) ? 1.0 : std::sin(kPi * x) / (kPi * x);
+    return sc * w;
+}
+
+// Tap j (bin k0 - 3 + j) as a polynomial of degree kTapDeg in t = 2 f - 1,
+// f in [0, 1) the fractional bin: Chebyshev interpolation at the Chebyshev
+// nodes, converted to monomial coefficients.
+void fit_taps(const DevScene &S, float out[8][kTapDeg + 1])
+{
+    const int N = kTapDeg + 1;
+    for (int j = 0; j < 8; ++j) {
+        double fv[N], cheb[N];
+        for (int i = 0; i < N; ++i) {
+            double t = std::cos(kPi * (i + 0.5) / N);
+            double f = 0.5 * (t + 1.0);
+            fv[i] = kaiser_sinc_host(S, (double)(j - 3) - f);
+        }
+        for (int k = 0; k < N; ++k) {
+            double acc = 0.0;
+            for (int i = 0; i < N; ++i) acc += fv[i] * std::cos(kPi * k * (i + 0.5) / N);
+            cheb[k] = acc * (k == 0 ? 1.0 : 2.0) / N;
+        }
+        // monomial coefficients of sum_k cheb[k] T_k(t)
+        double mono[N] = {0};
+        double tkm1[N] = {0}, tk[N] = {0}, tkp1[N];
+        tkm1[0] = 1.0;  // T_0
+        tk[1] = 1.0;    // T_1
+        for (int d = 0; d < N; ++d) mono[d] += cheb[0] * tkm1[d];
+        if (N > 1)
+            for (int d = 0; d < N; ++d) mono[d] += cheb[1] * tk[d];
+        for (int k = 2; k < N; ++k) {
+            for (int d = 0; d < N; ++d) tkp1[d] = -tkm1[d] + (d > 0 ? 2.0 * tk[d - 1] : 0.0);
+            for (int d = 0; d < N; ++d) mono[d] += cheb[k] * tkp1[d];
+            for (int d = 0; d < N; ++d) {
+                tkm1[d] = tk[d];
+                tk[d] = tkp1[d];
+            }
+        }
+        for (int d = 0; d < N; ++d) out[j][d] = (float)mono[d];
+    }
+}
+
+}  // namespace
+
+harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps, const std::vector<Wave> &waves)
+{
+    const harm_scene_desc &d = s->desc;
+    MixedTables &M = s->mixed;
+    const int nx = d.nx, ny = d.ny, np = d.n_pulses;
+    const int nw = (int)waves.size();
+    M.nb = mixed_batch_pulses();
+    M.n_batches = (np + M.nb - 1) / M.nb;
+    std::vector<float2> ex((size_t)std::max(nw, 1) * nx), ey((size_t)std::max(nw, 1) * ny);
+    for (int m = 0; m < nw; ++m) {
+        for (int ix = 0; ix < nx; ++ix) {
+            double a = waves[m].kx * (ix + 0.5 - 0.5 * nx) * d.facet_m;
+            ex[(size_t)m * nx + ix] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        for (int iy = 0; iy < ny; ++iy) {
+            double a = waves[m].ky * (iy + 0.5 - 0.5 * ny) * d.facet_m + waves[m].ph;
+            ey[(size_t)m * ny + iy] =
+                make_float2((float)(waves[m].amp * std::cos(a)), (float)(waves[m].amp * std::sin(a)));
+        }
+    }
+    // Taylor tables: E_{w,o} = e^{-i omega t_c} (-i omega)^o / o! about the batch
+    // centre t_c; fields eta (E), eta_x (i kx E), eta_y (i ky E).
+    std::vector<float> tau(np);
+    std::vector<float2> wt((size_t)M.n_batches * std::max(nw, 1) * 3 * kOrders);
+    for (int b = 0; b < M.n_batches; ++b) {
+        int first = b * M.nb, last = std::min(np, first + M.nb) - 1;
+        double tc = 0.5 * (ps[first].ts + ps[last].ts);
+        for (int n = first; n <= last; ++n) tau[n] = (float)(ps[n].ts - tc);
+        for (int m = 0; m < nw; ++m) {
+            double om = waves[m].om;
+            double er = std::cos(-om * tc), ei = std::sin(-om * tc);
+            for (int o = 0; o < kOrders; ++o) {
+                if (o > 0) {
+                    // multiply by (-i omega) / o
+                    double nr = om * ei / o, ni = -om * er / o;
+                    er = nr;
+                    ei = ni;
+                }
+                size_t base = (((size_t)b * nw + m) * 3) * kOrders + o;
+                wt[base] = make_float2((float)er, (float)ei);
+                // i k E = (-k Ei, k Er)
+                wt[base + kOrders] = make_float2((float)(-waves[m].kx * ei), (float)(waves[m].kx * er));
+                wt[base + 2 * kOrders] = make_float2((float)(-waves[m].ky * ei), (float)(waves[m].ky * er));
+            }
+        }
+    }
+    fit_taps(s->dev, M.tap);
+    if (upload_raw(s, ex, &M.ex) != cudaSuccess || upload_raw(s, ey, &M.ey) != cudaSuccess ||
+        upload_raw(s, wt, &M.wt) != cudaSuccess || upload_raw(s, tau, &M.tau) != cudaSuccess)
+        return HARM_E_CUDA;
+    return HARM_OK;
+}
+
+cudaError_t launch_generate(harm_scene *s, int n0, int np, void *state)
+{
+    if (s->desc.precision == HARM_PREC_FP64) return launch_generate_f64(s->dev, s->stream, n0, np, (double *)state);
+    return launch_generate_mixed(s->dev, s->mixed, s->stream, n0, np, (float *)state);
+}
+
+cudaError_t launch_accumulate(harm_scene *s, int n0, int np, void *iq, harm_dtype dtype)
+{
+    if (s->desc.precision == HARM_PREC_FP64) return launch_accumulate_f64(s->dev, s->stream, n0, np, iq, dtype);
+    return launch_accumulate_mixed(s->dev, s->mixed, s->stream, n0, np, iq, dtype);
+}
+
+cudaError_t launch_adjoint(harm_scene *, int, int, const void *, harm_dtype, double *, double *)
+{
+    return cudaErrorNotSupported;
+}
+
+}  // namespace harm

@@ -1,0 +1,76 @@
+// Internal data layout of the CUDA echo path (not part of the ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "harm.h"
+
+namespace harm {
+
+constexpr double kC = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxCh = HARM_MAX_CHANNELS;
+constexpr int kMaxI0Terms = 40;
+
+// State of one antenna phase centre for one pulse (FP64): position at its
+// transmit / receive time, steered antenna frame, and range to the scene centre.
+struct AntState {
+    double p[3];
+    double a[3];  // azimuth axis
+    double e[3];  // elevation axis
+    double rref;  // |p - 0|
+};
+
+// Per-pulse record (FP64, host-computed at scene creation).
+struct PulseState {
+    double t;   // transmit time t_n
+    double ts;  // bounce time at the scene centre
+    AntState tx;
+};
+
+// Per (pulse, channel) record: receive antenna state plus the reference phase
+// and range-bin offset of the scene centre.
+struct RxState {
+    AntState rx;
+    double psi;     // -K0 (R_t + R_r) reduced to (-pi, pi]
+    double p_ref;   // (R_t + R_r - R0_c) / dr: bin position of the scene centre
+};
+
+// Scene constants passed by value to every kernel.
+struct DevScene {
+    int nx, ny, nc, nr, np_total, nw, taps, static_surface, epoch_pulses;
+    int n_i0;               // terms of the Kaiser window series
+    double dx, k0, inv_lambda, inv_dr, area;
+    double tx_laz, tx_lel;
+    double rx_laz[kMaxCh], rx_lel[kMaxCh];
+    double sigma0_base, wind_mod, wcos, wsin, cur_u, cur_v;
+    uint64_t speckle_seed;
+    double i0c[kMaxI0Terms];  // window series coefficients / I0(beta)
+    // per-cell fields (device pointers owned by the caller) or null
+    int ncx, ncy;
+    double cell;
+    const double *cell_sigma0;
+    const double *cell_uv;
+    // scene tables (device)
+    const PulseState *pulses;  // [np_total]
+    const RxState *rx;         // [np_total][nc]
+    const double *kx, *ky, *om;  // [nw]
+    const double2 *ex;          // [nw][nx]   e^{i kx x}
+    const double2 *ey;          // [nw][ny]   a e^{i phi} e^{i ky y}
+    const double2 *tt;          // [nw][np_total] e^{-i omega t_s}
+    unsigned int *flags;        // device error / overflow counters [4]
+};
+
+// Mixed-precision tables (FP32 separable waves, Taylor time tables).
+struct DevMixed {
+    int nb;          // pulses per batch
+    int n_order;     // Taylor orders in time (M + 1)
+    int n_batches;
+    const float2 *ex;   // [nw][nx]
+    const float2 *ey;   // [nw][ny]
+    const float4 *wt;   // [n_batches][nw][n_order] : (E.re, E.im, omega-free k terms packed)
+    const float *tau;   // [np_total] t_s(n) - t_centre(batch(n))
+    const float *kx, *ky; // [nw]
+};
+
+}  // namespace harm

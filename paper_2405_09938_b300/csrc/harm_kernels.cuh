@@ -1,0 +1,66 @@
+// Internal interface between the host core and the kernel translation units.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "harm.h"
+#include "harm_internal.cuh"
+
+namespace harm {
+
+// Mixed-precision path tables (FP32 separable waves and the Taylor-in-time
+// tables of each pulse batch, plus the tap polynomials).
+constexpr int kTapDeg = 12;     // degree of each tap polynomial in t = 2f - 1
+constexpr int kOrders = 5;      // Taylor orders in time: tau^0 .. tau^4
+
+struct MixedTables {
+    int nb = 0;             // pulses per batch (time-Taylor expansion window)
+    int n_batches = 0;
+    int tile_x = 32, tile_y = 16;
+    const float2 *ex = nullptr;   // [nw][nx]          e^{i kx x}
+    const float2 *ey = nullptr;   // [nw][ny]          a e^{i phi} e^{i ky y}
+    const float2 *wt = nullptr;   // [n_batches][nw][3][kOrders] Taylor coefficients
+    const float *tau = nullptr;   // [np_total] t_s(n) - t_centre(batch)
+    float tap[8][kTapDeg + 1];    // Kaiser-sinc tap h(j - f), j = -3..4, monomials in t
+};
+
+}  // namespace harm
+
+struct harm_scene {
+    harm_scene_desc desc{};
+    std::vector<harm_antenna> rx;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    harm::DevScene dev{};
+    harm::MixedTables mixed{};
+    std::vector<void *> allocs;
+    std::vector<double> r0;
+    int64_t nf = 0;
+    int nw = 0;
+};
+
+namespace harm {
+
+struct Wave {
+    double kx, ky, om, amp, ph;
+};
+
+harm_status build_scene_tables(harm_scene *s);
+harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps, const std::vector<Wave> &waves);
+
+cudaError_t launch_generate(harm_scene *s, int n0, int np, void *state);
+cudaError_t launch_accumulate(harm_scene *s, int n0, int np, void *iq, harm_dtype dtype);
+cudaError_t launch_adjoint(harm_scene *s, int n0, int np, const void *resid, harm_dtype dtype, double *g_sigma0,
+                           double *g_uv);
+
+// FP64 path
+cudaError_t launch_generate_f64(const DevScene &S, cudaStream_t st, int n0, int np, double *state);
+cudaError_t launch_accumulate_f64(const DevScene &S, cudaStream_t st, int n0, int np, void *iq, harm_dtype dtype);
+// mixed path
+cudaError_t launch_generate_mixed(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np,
+                                  float *state);
+cudaError_t launch_accumulate_mixed(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np,
+                                    void *iq, harm_dtype dtype);
+
+}  // namespace harm

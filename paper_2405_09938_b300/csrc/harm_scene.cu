@@ -1,0 +1,545 @@
+// Host core of the echo library: descriptor validation, FP64 precompute of the
+// wave table and per-pulse platform state, device tables, and the C ABI.
+//
+// Everything computed here is per scene or per pulse (O(n_pulses x n_channels +
+// n_waves x (nx + ny + n_pulses))); all per-facet work runs in the kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "harm.h"
+#include "harm_internal.cuh"
+#include "harm_kernels.cuh"
+#include "philox.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+harm_status fail(harm_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+harm_status cuda_fail(cudaError_t e, const char *what)
+{
+    cudaGetLastError();  // clear a sticky launch error where possible
+    return fail(e == cudaErrorMemoryAllocation ? HARM_E_OOM : HARM_E_CUDA, "%s: %s (%s)", what,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define HARM_CUDA(call, what)                      \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool finite3(const double v[3]) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+double norm3(const double v[3]) { return std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); }
+
+void ant_pos(const harm_antenna &a, double t, double p[3])
+{
+    for (int i = 0; i < 3; ++i) p[i] = a.pos0[i] + a.vel[i] * t;
+}
+
+// Frame of an antenna steered to the scene centre: boresight toward the origin,
+// azimuth axis = velocity with its boresight part removed, elevation = b x a.
+void steer(const harm_antenna &ant, const double p[3], harm::AntState &s)
+{
+    double r = norm3(p);
+    double b[3] = {-p[0] / r, -p[1] / r, -p[2] / r};
+    double vb = ant.vel[0] * b[0] + ant.vel[1] * b[1] + ant.vel[2] * b[2];
+    double t[3] = {ant.vel[0] - vb * b[0], ant.vel[1] - vb * b[1], ant.vel[2] - vb * b[2]};
+    double tn = norm3(t);
+    for (int i = 0; i < 3; ++i) {
+        s.p[i] = p[i];
+        s.a[i] = t[i] / tn;
+    }
+    s.e[0] = b[1] * s.a[2] - b[2] * s.a[1];
+    s.e[1] = b[2] * s.a[0] - b[0] * s.a[2];
+    s.e[2] = b[0] * s.a[1] - b[1] * s.a[0];
+    s.rref = r;
+}
+
+// -K0 R reduced to (-pi, pi]: the phase in cycles is -f0 R / c; its fractional
+// part is taken in extended precision.
+double reduced_phase(double f0, double r)
+{
+    long double cyc = -(long double)f0 * (long double)r / (long double)harm::kC;
+    long double fr = cyc - std::floor(cyc + 0.5L);
+    return (double)(fr * 2.0L * (long double)harm::kPi);
+}
+
+struct PulseGeo {
+    harm::PulseState ps;
+    std::vector<harm::RxState> rx;
+};
+
+// Pulse n: transmit at t_n; the surface is sampled at the bounce time
+// t_s = t_n + R_t / c; the receive time solves t_r = t_s + R_r(t_r) / c by three
+// fixed-point steps started at t_s.
+void pulse_geometry(const harm_scene_desc &d, const std::vector<harm_antenna> &rx, int n,
+                    harm::PulseState &ps, harm::RxState *rs)
+{
+    ps.t = (double)n / d.prf_hz;
+    double p[3];
+    ant_pos(d.tx, ps.t, p);
+    steer(d.tx, p, ps.tx);
+    ps.ts = ps.t + ps.tx.rref / harm::kC;
+    for (int c = 0; c < d.n_channels; ++c) {
+        double tr = ps.ts;
+        for (int it = 0; it < 3; ++it) {
+            ant_pos(rx[c], tr, p);
+            tr = ps.ts + norm3(p) / harm::kC;
+        }
+        ant_pos(rx[c], tr, p);
+        steer(rx[c], p, rs[c].rx);
+    }
+}
+
+// JONSWAP spectrum with fetch-limited peak frequency and Phillips constant.
+double jonswap(double w, double u10, double fetch, double gamma)
+{
+    const double g = 9.80665;
+    double xt = g * fetch / (u10 * u10);
+    double wp = 22.0 * (g / u10) / std::cbrt(xt);
+    double alpha = 0.076 * std::pow(xt, -0.22);
+    double sig = w > wp ? 0.09 : 0.07;
+    double dw = (w - wp) / (sig * wp);
+    double shape = std::exp(-0.5 * dw * dw);
+    double q = wp / w;
+    return alpha * g * g / (w * w * w * w * w) * std::exp(-1.25 * q * q * q * q) * std::pow(gamma, shape);
+}
+
+double peak_omega(double u10, double fetch)
+{
+    const double g = 9.80665;
+    return 22.0 * (g / u10) / std::cbrt(g * fetch / (u10 * u10));
+}
+
+// Linear-wave grid: log-spaced frequency bins on [0.7, 2.5] x peak (geometric
+// centres), equally spaced directions about the wind, cos^2s spreading,
+// amplitude from the spectral energy of each cell, Philox phase.
+std::vector<harm::Wave> wave_grid(const harm_scene_desc &d)
+{
+    std::vector<harm::Wave> w;
+    if (d.n_omega <= 0 || d.n_theta <= 0 || d.static_surface) return w;
+    const double g = 9.80665;
+    double wp = peak_omega(d.u10, d.fetch_m);
+    double lo = 0.7 * wp, ratio = 2.5 / 0.7;
+    double dth = 2.0 * harm::kPi / d.n_theta;
+    double s = d.spread_s;
+    double norm = std::exp2(2.0 * s - 1.0) * std::exp(2.0 * std::lgamma(s + 1.0) - std::lgamma(2.0 * s + 1.0)) / harm::kPi;
+    for (int i = 0; i < d.n_omega; ++i) {
+        double e0 = lo * std::pow(ratio, (double)i / d.n_omega);
+        double e1 = lo * std::pow(ratio, (double)(i + 1) / d.n_omega);
+        double om = std::sqrt(e0 * e1);
+        double sw = jonswap(om, d.u10, d.fetch_m, d.gamma);
+        double k = om * om / g;
+        for (int j = 0; j < d.n_theta; ++j) {
+            int m = i * d.n_theta + j;
+            double rel = -harm::kPi + (j + 0.5) * dth;
+            double th = d.wind_dir_rad + rel;
+            double spread = norm * std::pow(std::cos(0.5 * rel), 2.0 * s);
+            harm::U32x4 r = harm::philox_stream(d.wave_seed, harm::kStreamWave, (uint32_t)m, 0u);
+            harm::Wave v;
+            v.kx = k * std::cos(th);
+            v.ky = k * std::sin(th);
+            v.om = om;
+            v.amp = std::sqrt(2.0 * sw * (e1 - e0) * spread * dth);
+            v.ph = 2.0 * harm::kPi * ((double)r.x * 0x1p-32);
+            w.push_back(v);
+        }
+    }
+    return w;
+}
+
+harm_status validate(const harm_scene_desc *d)
+{
+    if (!d) return fail(HARM_E_INVALID, "desc is NULL");
+    if (d->abi_version != HARM_ABI_VERSION)
+        return fail(HARM_E_INVALID, "abi_version %u, library is %u", d->abi_version, HARM_ABI_VERSION);
+    if (d->struct_size != sizeof(harm_scene_desc))
+        return fail(HARM_E_INVALID, "struct_size %u, library expects %zu", d->struct_size, sizeof(harm_scene_desc));
+    if (!(d->f0_hz > 0 && std::isfinite(d->f0_hz)) || !(d->fs_hz > 0 && std::isfinite(d->fs_hz)) ||
+        !(d->prf_hz > 0 && std::isfinite(d->prf_hz)))
+        return fail(HARM_E_INVALID, "f0, fs and prf must be positive and finite");
+    if (d->n_pulses < 1 || d->n_pulses > (1 << 24)) return fail(HARM_E_INVALID, "n_pulses out of range");
+    if (d->n_range < 1 || d->n_range > (1 << 24)) return fail(HARM_E_INVALID, "n_range out of range");
+    if (d->n_channels < 1 || d->n_channels > HARM_MAX_CHANNELS)
+        return fail(HARM_E_INVALID, "n_channels must be 1..%d", HARM_MAX_CHANNELS);
+    if (!d->rx) return fail(HARM_E_INVALID, "rx is NULL");
+    if (d->nx < 1 || d->ny < 1) return fail(HARM_E_INVALID, "facet grid must be at least 1 x 1");
+    if ((int64_t)d->nx * (int64_t)d->ny > 0xFFFFFFFFll)
+        return fail(HARM_E_INVALID, "more than 2^32 - 1 facets");
+    if (!(d->facet_m > 0 && std::isfinite(d->facet_m))) return fail(HARM_E_INVALID, "facet_m must be positive");
+    if (d->n_omega < 0 || d->n_theta < 0 || (d->n_omega == 0) != (d->n_theta == 0))
+        return fail(HARM_E_INVALID, "n_omega and n_theta must both be 0 or both positive");
+    if ((int64_t)d->n_omega * d->n_theta > 4096) return fail(HARM_E_INVALID, "more than 4096 wave components");
+    if (d->n_omega > 0 && !d->static_surface) {
+        if (!(d->u10 > 0) || !(d->fetch_m > 0) || !(d->gamma >= 1.0) || !(d->spread_s > 0) ||
+            !std::isfinite(d->wind_dir_rad))
+            return fail(HARM_E_INVALID, "sea-state parameters out of range");
+    }
+    if (!std::isfinite(d->wind_dir_rad) || !std::isfinite(d->current_u) || !std::isfinite(d->current_v))
+        return fail(HARM_E_INVALID, "wind direction and current must be finite");
+    if (!(d->sigma0_base >= 0 && std::isfinite(d->sigma0_base)) || !std::isfinite(d->wind_mod))
+        return fail(HARM_E_INVALID, "sigma0_base / wind_mod out of range");
+    if (d->epoch_pulses < 0) return fail(HARM_E_INVALID, "epoch_pulses must be >= 0");
+    if (d->taps != 1 && d->taps != 8) return fail(HARM_E_UNSUPPORTED, "taps must be 1 or 8");
+    if (!(d->kaiser_beta >= 0 && d->kaiser_beta <= 20)) return fail(HARM_E_INVALID, "kaiser_beta must be in [0, 20]");
+    if (d->precision != HARM_PREC_FP64 && d->precision != HARM_PREC_MIXED)
+        return fail(HARM_E_INVALID, "unknown precision %d", d->precision);
+    const harm_antenna *ants[1 + HARM_MAX_CHANNELS];
+    ants[0] = &d->tx;
+    for (int c = 0; c < d->n_channels; ++c) ants[1 + c] = &d->rx[c];
+    for (int i = 0; i <= d->n_channels; ++i) {
+        const harm_antenna &a = *ants[i];
+        if (!finite3(a.pos0) || !finite3(a.vel)) return fail(HARM_E_INVALID, "antenna %d: non-finite state", i);
+        if (!(a.len_az > 0) || !(a.len_el > 0)) return fail(HARM_E_INVALID, "antenna %d: lengths must be positive", i);
+        if (!(a.pos0[2] > 0)) return fail(HARM_E_INVALID, "antenna %d must be above the surface", i);
+        double v = norm3(a.vel);
+        double p = norm3(a.pos0);
+        double cross[3] = {a.pos0[1] * a.vel[2] - a.pos0[2] * a.vel[1], a.pos0[2] * a.vel[0] - a.pos0[0] * a.vel[2],
+                           a.pos0[0] * a.vel[1] - a.pos0[1] * a.vel[0]};
+        if (!(v > 0) || norm3(cross) < 1e-9 * v * p)
+            return fail(HARM_E_INVALID, "antenna %d: velocity must be nonzero and not along the line of sight", i);
+    }
+    return HARM_OK;
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T>
+harm_status upload(harm_scene *s, const std::vector<T> &h, const T **out)
+{
+    *out = nullptr;
+    if (h.empty()) return HARM_OK;
+    void *p = nullptr;
+    HARM_CUDA(cudaMalloc(&p, h.size() * sizeof(T)), "cudaMalloc scene table");
+    s->allocs.push_back(p);
+    HARM_CUDA(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s->stream),
+              "upload scene table");
+    *out = (const T *)p;
+    return HARM_OK;
+}
+
+void free_scene(harm_scene *s)
+{
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    for (void *p : s->allocs) cudaFree(p);
+    delete s;
+}
+
+harm_status check_window(const harm_scene *s, int32_t n0, int32_t np)
+{
+    if (!s) return fail(HARM_E_INVALID, "scene is NULL");
+    if (np < 0 || n0 < 0 || (int64_t)n0 + np > s->desc.n_pulses)
+        return fail(HARM_E_INVALID, "pulse window [%d, %d) outside [0, %d)", n0, n0 + np, s->desc.n_pulses);
+    return HARM_OK;
+}
+
+harm_status check_device(const harm_scene *s)
+{
+    int dev = -1;
+    HARM_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != s->device) return fail(HARM_E_INVALID, "scene lives on device %d, current device is %d", s->device, dev);
+    return HARM_OK;
+}
+
+harm_status check_ptr(const void *p, const char *what)
+{
+    if (!p) return fail(HARM_E_INVALID, "%s is NULL", what);
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes");
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(HARM_E_INVALID, "%s is not device memory", what);
+    return HARM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *harm_last_error(void) { return g_last_error.c_str(); }
+
+harm_status harm_scene_create(const harm_scene_desc *desc, void *cuda_stream, harm_scene **out)
+{
+    if (!out) return fail(HARM_E_INVALID, "out is NULL");
+    *out = nullptr;
+    harm_status st = validate(desc);
+    if (st != HARM_OK) return st;
+    harm_scene *s = new (std::nothrow) harm_scene;
+    if (!s) return fail(HARM_E_OOM, "host allocation failed");
+    s->desc = *desc;
+    s->rx.assign(desc->rx, desc->rx + desc->n_channels);
+    s->desc.rx = nullptr;
+    s->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) {
+        delete s;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    st = harm::build_scene_tables(s);
+    if (st != HARM_OK) {
+        std::string msg = g_last_error;
+        free_scene(s);
+        g_last_error = msg;
+        return st;
+    }
+    *out = s;
+    return HARM_OK;
+}
+
+harm_status harm_scene_destroy(harm_scene *scene)
+{
+    free_scene(scene);
+    return HARM_OK;
+}
+
+harm_status harm_scene_query(const harm_scene *s, harm_scene_info *info)
+{
+    if (!s || !info) return fail(HARM_E_INVALID, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n_facets = s->nf;
+    info->n_pulses = s->desc.n_pulses;
+    info->n_range = s->desc.n_range;
+    info->n_channels = s->desc.n_channels;
+    info->n_waves = s->nw;
+    info->precision = s->desc.precision;
+    info->pulse_batch = s->mixed.nb;
+    info->range_bin_m = harm::kC / s->desc.fs_hz;
+    for (int c = 0; c < s->desc.n_channels; ++c) info->range_start_m[c] = s->r0[c];
+    return HARM_OK;
+}
+
+harm_status harm_scene_set_cells(harm_scene *s, int32_t ncx, int32_t ncy, double cell_m, const double *sigma0_dev,
+                                 const double *uv_dev)
+{
+    if (!s) return fail(HARM_E_INVALID, "scene is NULL");
+    if (ncx == 0) {
+        s->dev.ncx = s->dev.ncy = 0;
+        s->dev.cell_sigma0 = s->dev.cell_uv = nullptr;
+        return HARM_OK;
+    }
+    if (ncx < 1 || ncy < 1 || !(cell_m > 0) || (int64_t)ncx * ncy > (1 << 24))
+        return fail(HARM_E_INVALID, "bad cell grid %d x %d of %g m", ncx, ncy, cell_m);
+    if (sigma0_dev) {
+        harm_status st = check_ptr(sigma0_dev, "sigma0_dev");
+        if (st != HARM_OK) return st;
+    }
+    if (uv_dev) {
+        harm_status st = check_ptr(uv_dev, "uv_dev");
+        if (st != HARM_OK) return st;
+    }
+    s->dev.ncx = ncx;
+    s->dev.ncy = ncy;
+    s->dev.cell = cell_m;
+    s->dev.cell_sigma0 = sigma0_dev;
+    s->dev.cell_uv = uv_dev;
+    return HARM_OK;
+}
+
+harm_status harm_facets_generate(harm_scene *s, int32_t n0, int32_t np, void *state_dev)
+{
+    harm_status st = check_window(s, n0, np);
+    if (st != HARM_OK) return st;
+    if ((st = check_device(s)) != HARM_OK) return st;
+    if (np == 0) return HARM_OK;
+    if ((st = check_ptr(state_dev, "state_dev")) != HARM_OK) return st;
+    cudaError_t e = harm::launch_generate(s, n0, np, state_dev);
+    if (e != cudaSuccess) return cuda_fail(e, "facet generator launch");
+    return HARM_OK;
+}
+
+harm_status harm_echo_accumulate(harm_scene *s, int32_t n0, int32_t np, void *iq_dev, harm_dtype dtype,
+                                 int32_t zero_first)
+{
+    harm_status st = check_window(s, n0, np);
+    if (st != HARM_OK) return st;
+    if ((st = check_device(s)) != HARM_OK) return st;
+    if (dtype != HARM_C64 && dtype != HARM_C128) return fail(HARM_E_INVALID, "unknown dtype %d", (int)dtype);
+    if (np == 0) return HARM_OK;
+    if ((st = check_ptr(iq_dev, "iq_dev")) != HARM_OK) return st;
+    size_t bytes = (size_t)s->desc.n_channels * np * s->desc.n_range * (dtype == HARM_C64 ? 8 : 16);
+    if (zero_first) HARM_CUDA(cudaMemsetAsync(iq_dev, 0, bytes, s->stream), "cudaMemsetAsync iq");
+    cudaError_t e = harm::launch_accumulate(s, n0, np, iq_dev, dtype);
+    if (e != cudaSuccess) return cuda_fail(e, "echo accumulator launch");
+    return HARM_OK;
+}
+
+harm_status harm_echo_adjoint(harm_scene *s, int32_t n0, int32_t np, const void *resid_dev, harm_dtype dtype,
+                              double *grad_sigma0_dev, double *grad_uv_dev)
+{
+    harm_status st = check_window(s, n0, np);
+    if (st != HARM_OK) return st;
+    if ((st = check_device(s)) != HARM_OK) return st;
+    if (dtype != HARM_C64 && dtype != HARM_C128) return fail(HARM_E_INVALID, "unknown dtype %d", (int)dtype);
+    if (s->dev.ncx == 0) return fail(HARM_E_INVALID, "adjoint needs per-cell fields (harm_scene_set_cells)");
+    if (np == 0) return HARM_OK;
+    if ((st = check_ptr(resid_dev, "resid_dev")) != HARM_OK) return st;
+    if (grad_sigma0_dev && (st = check_ptr(grad_sigma0_dev, "grad_sigma0_dev")) != HARM_OK) return st;
+    if (grad_uv_dev && (st = check_ptr(grad_uv_dev, "grad_uv_dev")) != HARM_OK) return st;
+    cudaError_t e = harm::launch_adjoint(s, n0, np, resid_dev, dtype, grad_sigma0_dev, grad_uv_dev);
+    if (e == cudaErrorNotSupported) return fail(HARM_E_UNSUPPORTED, "adjoint not available for this scene");
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+    return HARM_OK;
+}
+
+harm_status harm_scene_sync(harm_scene *s)
+{
+    if (!s) return fail(HARM_E_INVALID, "scene is NULL");
+    HARM_CUDA(cudaStreamSynchronize(s->stream), "cudaStreamSynchronize");
+    unsigned int flags[4] = {0, 0, 0, 0};
+    HARM_CUDA(cudaMemcpy(flags, s->dev.flags, sizeof(flags), cudaMemcpyDeviceToHost), "read device flags");
+    HARM_CUDA(cudaMemset(s->dev.flags, 0, sizeof(flags)), "clear device flags");
+    if (flags[0]) return fail(HARM_E_TIMEOUT, "a bounded device wait gave up (%u times)", flags[0]);
+    if (flags[1]) return fail(HARM_E_CUDA, "device bounds check failed (%u times)", flags[1]);
+    return HARM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Scene tables
+// ---------------------------------------------------------------------------
+namespace harm {
+
+harm_status build_scene_tables(harm_scene *s)
+{
+    const harm_scene_desc &d = s->desc;
+    const int np = d.n_pulses, nc = d.n_channels, nx = d.nx, ny = d.ny;
+    s->nf = (int64_t)nx * ny;
+    DevScene &v = s->dev;
+    v.nx = nx;
+    v.ny = ny;
+    v.nc = nc;
+    v.nr = d.n_range;
+    v.np_total = np;
+    v.taps = d.taps;
+    v.static_surface = d.static_surface ? 1 : 0;
+    v.epoch_pulses = d.epoch_pulses;
+    v.dx = d.facet_m;
+    double lambda = kC / d.f0_hz;
+    v.k0 = 2.0 * kPi / lambda;
+    v.inv_lambda = 1.0 / lambda;
+    v.inv_dr = d.fs_hz / kC;
+    v.area = d.facet_m * d.facet_m;
+    v.tx_laz = d.tx.len_az;
+    v.tx_lel = d.tx.len_el;
+    for (int c = 0; c < nc; ++c) {
+        v.rx_laz[c] = s->rx[c].len_az;
+        v.rx_lel[c] = s->rx[c].len_el;
+    }
+    v.sigma0_base = d.sigma0_base;
+    v.wind_mod = d.wind_mod;
+    v.wcos = std::cos(d.wind_dir_rad);
+    v.wsin = std::sin(d.wind_dir_rad);
+    v.cur_u = d.current_u;
+    v.cur_v = d.current_v;
+    v.speckle_seed = d.speckle_seed;
+    // Kaiser window I0(beta sqrt(v)) / I0(beta) as a power series in v = 1 - (x/4)^2:
+    // coefficient k is (beta^2/4)^k / (k!)^2, divided by I0(beta) = sum of them.
+    {
+        double q = 0.25 * d.kaiser_beta * d.kaiser_beta;
+        double c[kMaxI0Terms];
+        double term = 1.0, sum = 0.0;
+        int n = 0;
+        for (; n < kMaxI0Terms; ++n) {
+            if (n > 0) term *= q / ((double)n * n);
+            c[n] = term;
+            sum += term;
+            if (n > 2 && term < 1e-18 * sum) {
+                ++n;
+                break;
+            }
+        }
+        v.n_i0 = n;
+        for (int k = 0; k < n; ++k) v.i0c[k] = c[k] / sum;
+    }
+
+    // per-pulse platform state
+    std::vector<PulseState> ps(np);
+    std::vector<RxState> rs((size_t)np * nc);
+    for (int n = 0; n < np; ++n) pulse_geometry(d, s->rx, n, ps[n], &rs[(size_t)n * nc]);
+    double dr = kC / d.fs_hz;
+    s->r0.resize(nc);
+    for (int c = 0; c < nc; ++c) {
+        const PulseState &pm = ps[np / 2];
+        const RxState &rm = rs[(size_t)(np / 2) * nc + c];
+        s->r0[c] = pm.tx.rref + rm.rx.rref - 0.5 * d.n_range * dr;
+    }
+    for (int n = 0; n < np; ++n)
+        for (int c = 0; c < nc; ++c) {
+            RxState &r = rs[(size_t)n * nc + c];
+            double rsum = ps[n].tx.rref + r.rx.rref;
+            r.psi = reduced_phase(d.f0_hz, rsum);
+            r.p_ref = (rsum - s->r0[c]) / dr;
+        }
+
+    // waves: separable phasor tables e^{i kx x}, a e^{i phi} e^{i ky y}, e^{-i omega t_s}
+    std::vector<Wave> waves = wave_grid(d);
+    int nw = (int)waves.size();
+    s->nw = nw;
+    v.nw = nw;
+    std::vector<double> kx(nw), ky(nw), om(nw);
+    std::vector<double2> ex((size_t)nw * nx), ey((size_t)nw * ny), tt((size_t)nw * np);
+    for (int m = 0; m < nw; ++m) {
+        kx[m] = waves[m].kx;
+        ky[m] = waves[m].ky;
+        om[m] = waves[m].om;
+        for (int ix = 0; ix < nx; ++ix) {
+            double x = (ix + 0.5 - 0.5 * nx) * d.facet_m;
+            double a = waves[m].kx * x;
+            ex[(size_t)m * nx + ix] = make_double2(std::cos(a), std::sin(a));
+        }
+        for (int iy = 0; iy < ny; ++iy) {
+            double y = (iy + 0.5 - 0.5 * ny) * d.facet_m;
+            double a = waves[m].ky * y + waves[m].ph;
+            ey[(size_t)m * ny + iy] = make_double2(waves[m].amp * std::cos(a), waves[m].amp * std::sin(a));
+        }
+        for (int n = 0; n < np; ++n) {
+            double a = -waves[m].om * ps[n].ts;
+            tt[(size_t)m * np + n] = make_double2(std::cos(a), std::sin(a));
+        }
+    }
+
+    harm_status st;
+    if ((st = upload(s, ps, &v.pulses)) != HARM_OK) return st;
+    if ((st = upload(s, rs, &v.rx)) != HARM_OK) return st;
+    if ((st = upload(s, kx, &v.kx)) != HARM_OK) return st;
+    if ((st = upload(s, ky, &v.ky)) != HARM_OK) return st;
+    if ((st = upload(s, om, &v.om)) != HARM_OK) return st;
+    if (d.precision == HARM_PREC_FP64) {
+        if ((st = upload(s, ex, &v.ex)) != HARM_OK) return st;
+        if ((st = upload(s, ey, &v.ey)) != HARM_OK) return st;
+        if ((st = upload(s, tt, &v.tt)) != HARM_OK) return st;
+    }
+    std::vector<unsigned int> flags(4, 0u);
+    const unsigned int *fl = nullptr;
+    if ((st = upload(s, flags, &fl)) != HARM_OK) return st;
+    v.flags = const_cast<unsigned int *>(fl);
+    if (d.precision == HARM_PREC_MIXED) {
+        st = build_mixed_tables(s, ps, waves);
+        if (st != HARM_OK) return fail(st, "mixed-precision table upload failed");
+    }
+    HARM_CUDA(cudaStreamSynchronize(s->stream), "scene upload");
+    return HARM_OK;
+}
+
+}  // namespace harm

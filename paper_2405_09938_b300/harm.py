@@ -1,0 +1,253 @@
+"""Thin ctypes binding of ``libharm.so`` (the C ABI declared in ``include/harm.h``).
+
+Argument marshalling only: every step of the echo path runs in the library's
+CUDA kernels. Torch tensors are used as device buffers and torch streams as CUDA
+streams. There is no CPU fallback: loading fails loudly when the library is
+missing or cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libharm.so")
+
+HARM_ABI_VERSION = 1
+HARM_MAX_CHANNELS = 16
+HARM_OK, HARM_E_INVALID, HARM_E_CUDA, HARM_E_OOM, HARM_E_TIMEOUT, HARM_E_UNSUPPORTED = range(6)
+HARM_C64, HARM_C128 = 0, 1
+HARM_PREC_FP64, HARM_PREC_MIXED = 0, 1
+STATUS_NAMES = {0: "HARM_OK", 1: "HARM_E_INVALID", 2: "HARM_E_CUDA", 3: "HARM_E_OOM",
+                4: "HARM_E_TIMEOUT", 5: "HARM_E_UNSUPPORTED"}
+
+
+class HarmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), msg))
+        self.status = status
+
+
+class harm_antenna(C.Structure):
+    _fields_ = [("pos0", C.c_double * 3), ("vel", C.c_double * 3),
+                ("len_az", C.c_double), ("len_el", C.c_double)]
+
+
+class harm_scene_desc(C.Structure):
+    _fields_ = [
+        ("abi_version", C.c_uint32), ("struct_size", C.c_uint32),
+        ("f0_hz", C.c_double), ("fs_hz", C.c_double), ("prf_hz", C.c_double),
+        ("n_pulses", C.c_int32), ("n_range", C.c_int32),
+        ("tx", harm_antenna),
+        ("n_channels", C.c_int32),
+        ("rx", C.POINTER(harm_antenna)),
+        ("nx", C.c_int32), ("ny", C.c_int32),
+        ("facet_m", C.c_double),
+        ("n_omega", C.c_int32), ("n_theta", C.c_int32),
+        ("u10", C.c_double), ("fetch_m", C.c_double), ("wind_dir_rad", C.c_double),
+        ("spread_s", C.c_double), ("gamma", C.c_double),
+        ("wave_seed", C.c_uint64),
+        ("current_u", C.c_double), ("current_v", C.c_double),
+        ("sigma0_base", C.c_double), ("wind_mod", C.c_double),
+        ("epoch_pulses", C.c_int32),
+        ("speckle_seed", C.c_uint64),
+        ("static_surface", C.c_int32),
+        ("taps", C.c_int32),
+        ("kaiser_beta", C.c_double),
+        ("precision", C.c_int32),
+    ]
+
+
+class harm_scene_info(C.Structure):
+    _fields_ = [("n_facets", C.c_int64), ("n_pulses", C.c_int32), ("n_range", C.c_int32),
+                ("n_channels", C.c_int32), ("n_waves", C.c_int32), ("precision", C.c_int32),
+                ("pulse_batch", C.c_int32), ("range_bin_m", C.c_double),
+                ("range_start_m", C.c_double * HARM_MAX_CHANNELS)]
+
+
+# Every function the header declares, with its ctypes signature.
+_VP = C.c_void_p
+SIGNATURES = {
+    "harm_scene_create": (C.c_int, [C.POINTER(harm_scene_desc), _VP, C.POINTER(_VP)]),
+    "harm_scene_destroy": (C.c_int, [_VP]),
+    "harm_scene_query": (C.c_int, [_VP, C.POINTER(harm_scene_info)]),
+    "harm_scene_set_cells": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP]),
+    "harm_facets_generate": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP]),
+    "harm_echo_accumulate": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP, C.c_int, C.c_int32]),
+    "harm_echo_adjoint": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP, C.c_int, _VP, _VP]),
+    "harm_scene_sync": (C.c_int, [_VP]),
+    "harm_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load ``libharm.so``; raise if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError("libharm.so not built at %s (run python -m paper_2405_09938_b300.build)"
+                              % path)
+        lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def harm_last_error() -> str:
+    return load_library().harm_last_error().decode()
+
+
+def _check(status):
+    if status != HARM_OK:
+        raise HarmError(status, harm_last_error())
+
+
+def _antenna(a):
+    s = harm_antenna()
+    for i in range(3):
+        s.pos0[i] = a["pos0"][i]
+        s.vel[i] = a["vel"][i]
+    s.len_az, s.len_el = a["len_az"], a["len_el"]
+    return s
+
+
+def make_desc(d: dict, precision: int):
+    """Marshal a scene dictionary (see :mod:`harm_scenes`) into harm_scene_desc.
+    Returns (desc, keepalive) -- the rx array must outlive the create call."""
+    rx = (harm_antenna * len(d["rx"]))(*[_antenna(a) for a in d["rx"]])
+    s = harm_scene_desc()
+    s.abi_version = HARM_ABI_VERSION
+    s.struct_size = C.sizeof(harm_scene_desc)
+    s.f0_hz, s.fs_hz, s.prf_hz = d["f0_hz"], d["fs_hz"], d["prf_hz"]
+    s.n_pulses, s.n_range = d["n_pulses"], d["n_range"]
+    s.tx = _antenna(d["tx"])
+    s.n_channels = len(d["rx"])
+    s.rx = C.cast(rx, C.POINTER(harm_antenna))
+    s.nx, s.ny, s.facet_m = d["nx"], d["ny"], d["facet_m"]
+    s.n_omega, s.n_theta = d["n_omega"], d["n_theta"]
+    s.u10, s.fetch_m, s.wind_dir_rad = d["u10"], d["fetch_m"], d["wind_dir_rad"]
+    s.spread_s, s.gamma, s.wave_seed = d["spread_s"], d["gamma"], d["wave_seed"]
+    s.current_u, s.current_v = d["current_u"], d["current_v"]
+    s.sigma0_base, s.wind_mod = d["sigma0_base"], d["wind_mod"]
+    s.epoch_pulses, s.speckle_seed = d["epoch_pulses"], d["speckle_seed"]
+    s.static_surface = d["static_surface"]
+    s.taps, s.kaiser_beta = d["taps"], d["kaiser_beta"]
+    s.precision = precision
+    return s, rx
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Scene:
+    """Owning handle of a ``harm_scene``."""
+
+    def __init__(self, ptr, desc: dict, precision: int, stream):
+        self._ptr = ptr
+        self.desc = desc
+        self.precision = precision
+        self.stream = stream
+        self._cells = None
+
+    @property
+    def handle(self):
+        if self._ptr is None:
+            raise HarmError(HARM_E_INVALID, "scene destroyed")
+        return self._ptr
+
+    def close(self):
+        if self._ptr is not None and _lib is not None:
+            _lib.harm_scene_destroy(self._ptr)
+        self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def harm_scene_create(desc: dict, precision: int = HARM_PREC_FP64, stream=None) -> Scene:
+    lib = load_library()
+    s, keep = make_desc(desc, precision)
+    out = C.c_void_p()
+    _check(lib.harm_scene_create(C.byref(s), C.c_void_p(_stream_handle(stream)), C.byref(out)))
+    del keep
+    return Scene(out, desc, precision, stream)
+
+
+def harm_scene_destroy(scene: Scene):
+    scene.close()
+
+
+def harm_scene_query(scene: Scene) -> dict:
+    info = harm_scene_info()
+    _check(load_library().harm_scene_query(scene.handle, C.byref(info)))
+    return {"n_facets": info.n_facets, "n_pulses": info.n_pulses, "n_range": info.n_range,
+            "n_channels": info.n_channels, "n_waves": info.n_waves, "precision": info.precision,
+            "pulse_batch": info.pulse_batch, "range_bin_m": info.range_bin_m,
+            "range_start_m": np.array(info.range_start_m[:info.n_channels])}
+
+
+def _dev_ptr(t, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise HarmError(HARM_E_INVALID, "%s must be a CUDA tensor" % what)
+    if not t.is_contiguous():
+        raise HarmError(HARM_E_INVALID, "%s must be contiguous" % what)
+    return C.c_void_p(t.data_ptr())
+
+
+def harm_scene_set_cells(scene: Scene, ncx, ncy, cell_m, sigma0=None, uv=None):
+    sp = _dev_ptr(sigma0, "sigma0") if sigma0 is not None else None
+    up = _dev_ptr(uv, "uv") if uv is not None else None
+    _check(load_library().harm_scene_set_cells(scene.handle, ncx, ncy, cell_m, sp, up))
+    scene._cells = (sigma0, uv)
+
+
+def harm_facets_generate(scene: Scene, n0: int, np_: int, state):
+    _check(load_library().harm_facets_generate(scene.handle, n0, np_, _dev_ptr(state, "state")))
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.complex64:
+        return HARM_C64
+    if t.dtype == torch.complex128:
+        return HARM_C128
+    raise HarmError(HARM_E_INVALID, "IQ tensors must be complex64 or complex128")
+
+
+def harm_echo_accumulate(scene: Scene, n0: int, np_: int, iq, zero_first: bool = True):
+    _check(load_library().harm_echo_accumulate(scene.handle, n0, np_, _dev_ptr(iq, "iq"),
+                                               _dtype_code(iq), 1 if zero_first else 0))
+
+
+def harm_echo_adjoint(scene: Scene, n0: int, np_: int, resid, grad_sigma0=None, grad_uv=None):
+    gs = _dev_ptr(grad_sigma0, "grad_sigma0") if grad_sigma0 is not None else None
+    gu = _dev_ptr(grad_uv, "grad_uv") if grad_uv is not None else None
+    _check(load_library().harm_echo_adjoint(scene.handle, n0, np_, _dev_ptr(resid, "resid"),
+                                            _dtype_code(resid), gs, gu))
+
+
+def harm_scene_sync(scene: Scene):
+    _check(load_library().harm_scene_sync(scene.handle))

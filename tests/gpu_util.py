@@ -1,0 +1,46 @@
+"""Helpers for the GPU parity tests: run the CUDA path through the C ABI and
+compare with the oracle."""
+import numpy as np
+
+from paper_2405_09938_b300 import harm
+
+
+def run_echo(desc, precision, n0, np_, dtype="c128", scene=None):
+    import torch
+    tdt = torch.complex128 if dtype == "c128" else torch.complex64
+    own = scene is None
+    if own:
+        scene = harm.harm_scene_create(desc, precision)
+    iq = torch.zeros((len(desc["rx"]), np_, desc["n_range"]), dtype=tdt, device="cuda")
+    harm.harm_echo_accumulate(scene, n0, np_, iq, zero_first=True)
+    harm.harm_scene_sync(scene)
+    out = iq.cpu().numpy()
+    if own:
+        scene.close()
+    return out
+
+
+def run_states(desc, precision, n0, np_):
+    import torch
+    scene = harm.harm_scene_create(desc, precision)
+    tdt = torch.float64 if precision == harm.HARM_PREC_FP64 else torch.float32
+    st = torch.zeros((np_, 3, desc["ny"], desc["nx"]), dtype=tdt, device="cuda")
+    harm.harm_facets_generate(scene, n0, np_, st)
+    harm.harm_scene_sync(scene)
+    out = st.cpu().numpy().astype(np.float64)
+    scene.close()
+    return out
+
+
+def rel_rms(got, want):
+    num = np.sum(np.abs(got - want) ** 2)
+    den = np.sum(np.abs(want) ** 2)
+    return float(np.sqrt(num / den)) if den > 0 else float(np.sqrt(num))
+
+
+def ati_phase_bias(got, want, a, b):
+    """wrap(arg sum IQ_a conj IQ_b (GPU) - same (oracle)) in rad."""
+    g = np.sum(got[a] * np.conj(got[b]))
+    w = np.sum(want[a] * np.conj(want[b]))
+    d = np.angle(g) - np.angle(w)
+    return float((d + np.pi) % (2 * np.pi) - np.pi)

@@ -1,0 +1,94 @@
+"""CPU checks of the C ABI: the library builds and loads, exports every function
+include/harm.h declares, and the ctypes mirror of every struct has the C layout."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2405_09938_b300 import build as harm_build
+from paper_2405_09938_b300 import harm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "harm.h")
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(harm_[a-z_]+)\s*\(", src)))
+
+
+def test_library_builds_and_loads():
+    path = harm_build.build()
+    assert os.path.exists(path)
+    lib = harm.load_library(path)
+    assert lib is not None
+
+
+def test_every_declared_symbol_exported():
+    lib = ctypes.CDLL(harm_build.build())
+    names = _declared_functions()
+    assert "harm_echo_accumulate" in names and "harm_scene_create" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(harm.SIGNATURES), "binding and header disagree"
+
+
+def test_last_error_without_gpu_work():
+    lib = harm.load_library(harm_build.build())
+    assert isinstance(lib.harm_last_error(), bytes)
+
+
+def _c_layout(struct, fields):
+    code = ['#include <stdio.h>', '#include <stddef.h>', '#include "harm.h"', 'int main(void){',
+            '  printf("%%zu\\n", sizeof(%s));' % struct]
+    for f in fields:
+        code.append('  printf("%%zu\\n", offsetof(%s, %s));' % (struct, f))
+    code.append("  return 0; }")
+    return "\n".join(code)
+
+
+@pytest.mark.parametrize("name,cls", [("harm_scene_desc", harm.harm_scene_desc),
+                                      ("harm_antenna", harm.harm_antenna),
+                                      ("harm_scene_info", harm.harm_scene_info)])
+def test_struct_layout_matches_header(tmp_path, name, cls):
+    fields = [f[0] for f in cls._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text(_c_layout(name, fields))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(cls)
+    for f, off in zip(fields, out[1:]):
+        assert getattr(cls, f).offset == off, f
+
+
+def test_invalid_descriptor_rejected_without_device_work():
+    """Validation runs on the host before any CUDA call."""
+    import harm_scenes as hs
+    lib = harm.load_library(harm_build.build())
+    d = hs.small_static()
+    s, keep = harm.make_desc(d, harm.HARM_PREC_FP64)
+    s.struct_size = 12
+    out = ctypes.c_void_p()
+    st = lib.harm_scene_create(ctypes.byref(s), None, ctypes.byref(out))
+    assert st == harm.HARM_E_INVALID
+    assert b"struct_size" in lib.harm_last_error()
+    assert out.value is None
+    s, keep = harm.make_desc(d, harm.HARM_PREC_FP64)
+    s.taps = 5
+    assert lib.harm_scene_create(ctypes.byref(s), None, ctypes.byref(out)) == harm.HARM_E_UNSUPPORTED
+    s, keep = harm.make_desc(d, harm.HARM_PREC_FP64)
+    s.n_channels = 0
+    assert lib.harm_scene_create(ctypes.byref(s), None, ctypes.byref(out)) == harm.HARM_E_INVALID
+    s, keep = harm.make_desc(d, harm.HARM_PREC_FP64)
+    s.tx.pos0[2] = -1.0
+    assert lib.harm_scene_create(ctypes.byref(s), None, ctypes.byref(out)) == harm.HARM_E_INVALID
+    assert lib.harm_scene_create(None, None, ctypes.byref(out)) == harm.HARM_E_INVALID
+    # NULL scene handles
+    assert lib.harm_echo_accumulate(None, 0, 1, None, 0, 1) == harm.HARM_E_INVALID
+    assert lib.harm_scene_sync(None) == harm.HARM_E_INVALID
+    assert lib.harm_scene_destroy(None) == harm.HARM_OK

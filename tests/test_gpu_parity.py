@@ -1,0 +1,187 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded scenes, element by element.
+
+Tolerances (IQ relative RMS over all compared samples):
+  * FP64 path: 1e-7. The only differences are rounding order, the offset form of
+    the ranges and the wave phasor tables; the bound on the path is 1e-5.
+  * Mixed path: 1e-4 (FP32 phase, patterns, taps and accumulation).
+"""
+import numpy as np
+import pytest
+
+import harm_scenes as hs
+import oracle
+from paper_2405_09938_b300 import harm
+from tests.gpu_util import ati_phase_bias, rel_rms, run_echo, run_states
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-7
+TOL_MIXED = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.init()
+
+
+def small_wave_scene(n_pulses=64, nx=48, ny=40, n_range=1024):
+    return hs.ati_scene(n_pulses=n_pulses, nx=nx, ny=ny, n_range=n_range)
+
+
+# ------------------------------------------------------------------ generator
+def test_generator_fp64_matches_oracle():
+    d = small_wave_scene(n_pulses=64, nx=37, ny=23)
+    got = run_states(d, harm.HARM_PREC_FP64, 10, 5)
+    for i, n in enumerate(range(10, 15)):
+        want = oracle.facet_states(d, n)
+        assert np.abs(got[i] - want).max() < 1e-11
+
+
+def test_generator_mixed_matches_oracle():
+    d = small_wave_scene(n_pulses=100, nx=70, ny=33)
+    got = run_states(d, harm.HARM_PREC_MIXED, 30, 40)
+    for i, n in [(0, 30), (1, 31), (17, 47), (39, 69)]:
+        want = oracle.facet_states(d, n)
+        err = np.abs(got[i] - want)
+        assert err[0].max() < 2e-6      # height [m]
+        assert err[1:].max() < 2e-6     # slopes
+
+
+# ------------------------------------------------------------------ FP64 path
+@pytest.mark.parametrize("taps", [8, 1])
+def test_static_patch_fp64(taps):
+    d = hs.small_static()
+    d["taps"] = taps
+    got = run_echo(d, harm.HARM_PREC_FP64, 0, 64, "c128")
+    want = oracle.echo(d, list(range(64)))
+    assert rel_rms(got, want) < TOL_FP64
+
+
+def test_wave_scene_fp64_all_channels():
+    d = small_wave_scene()
+    got = run_echo(d, harm.HARM_PREC_FP64, 0, 64, "c128")
+    want = oracle.echo(d, list(range(64)))
+    assert got.shape == want.shape == (6, 64, 1024)
+    assert rel_rms(got, want) < TOL_FP64
+    for c in range(6):
+        assert rel_rms(got[c], want[c]) < TOL_FP64
+
+
+def test_fp64_path_c64_output():
+    d = hs.small_static()
+    got = run_echo(d, harm.HARM_PREC_FP64, 0, 64, "c64")
+    want = oracle.echo(d, list(range(64)))
+    assert rel_rms(got, want) < 1e-6
+
+
+# ------------------------------------------------------------------ mixed path
+@pytest.mark.parametrize("taps", [8, 1])
+def test_static_patch_mixed(taps):
+    d = hs.small_static()
+    d["taps"] = taps
+    got = run_echo(d, harm.HARM_PREC_MIXED, 0, 64, "c64")
+    want = oracle.echo(d, list(range(64)))
+    assert rel_rms(got, want) < TOL_MIXED
+
+
+def test_wave_scene_mixed_errors():
+    d = small_wave_scene()
+    got = run_echo(d, harm.HARM_PREC_MIXED, 0, 64, "c64")
+    want = oracle.echo(d, list(range(64)))
+    err = rel_rms(got, want)
+    assert err < TOL_MIXED, err
+    for sat in (0, 3):
+        for a, b in ((0, 1), (1, 2), (0, 2)):
+            assert abs(ati_phase_bias(got, want, sat + a, sat + b)) < 1e-4
+
+
+def test_mixed_c128_output():
+    d = small_wave_scene(n_pulses=40)
+    got = run_echo(d, harm.HARM_PREC_MIXED, 0, 40, "c128")
+    want = oracle.echo(d, list(range(40)))
+    assert rel_rms(got, want) < TOL_MIXED
+
+
+# ------------------------------------------------------------------ edges
+def test_ragged_grid_and_unaligned_pulse_window():
+    # grid not a multiple of the tiles, window crossing batch and epoch edges
+    d = small_wave_scene(n_pulses=120, nx=45, ny=19)
+    n0, np_ = 29, 45
+    want = oracle.echo(d, list(range(n0, n0 + np_)))
+    for prec, tol, dt in ((harm.HARM_PREC_FP64, TOL_FP64, "c128"), (harm.HARM_PREC_MIXED, TOL_MIXED, "c64")):
+        got = run_echo(d, prec, n0, np_, dt)
+        assert rel_rms(got, want) < tol
+
+
+def test_echo_partly_outside_range_window():
+    # a short range window cuts the echo: taps outside [0, n_range) are dropped
+    d = small_wave_scene(n_pulses=16, nx=64, ny=64, n_range=1024)
+    full = oracle.echo(d, list(range(16)))
+    nz = np.nonzero(np.abs(full).sum(axis=(0, 1)))[0]
+    lo, hi = nz.min(), nz.max()
+    # a window narrower than the echo (R0 = R_ref - n_range/2 dr stays centred)
+    cut = dict(d, n_range=max(8, int((hi - lo) // 2)))
+    want = oracle.echo(cut, list(range(16)))
+    assert np.abs(want[:, :, 0]).max() > 0 and np.abs(want[:, :, -1]).max() > 0
+    for prec, tol, dt in ((harm.HARM_PREC_FP64, TOL_FP64, "c128"), (harm.HARM_PREC_MIXED, TOL_MIXED, "c64")):
+        got = run_echo(cut, prec, 0, 16, dt)
+        assert rel_rms(got, want) < tol
+
+
+def test_single_facet_and_single_pulse():
+    d = hs.small_static(n_pulses=3)
+    d.update(nx=1, ny=1)
+    want = oracle.echo(d, [2])
+    for prec, tol, dt in ((harm.HARM_PREC_FP64, TOL_FP64, "c128"), (harm.HARM_PREC_MIXED, TOL_MIXED, "c64")):
+        got = run_echo(d, prec, 2, 1, dt)
+        assert rel_rms(got, want) < tol
+
+
+def test_empty_window_is_noop():
+    import torch
+    d = hs.small_static()
+    scene = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
+    iq = torch.full((1, 1, 512), 7.0, dtype=torch.complex64, device="cuda")
+    harm.harm_echo_accumulate(scene, 5, 0, iq)
+    harm.harm_scene_sync(scene)
+    assert torch.all(iq == 7.0)
+    scene.close()
+
+
+def test_accumulate_without_zeroing_adds():
+    import torch
+    d = hs.small_static()
+    scene = harm.harm_scene_create(d, harm.HARM_PREC_FP64)
+    iq = torch.zeros((1, 8, 512), dtype=torch.complex128, device="cuda")
+    harm.harm_echo_accumulate(scene, 0, 8, iq, zero_first=True)
+    harm.harm_echo_accumulate(scene, 0, 8, iq, zero_first=False)
+    harm.harm_scene_sync(scene)
+    want = oracle.echo(d, list(range(8)))
+    assert rel_rms(iq.cpu().numpy(), 2 * want) < TOL_FP64
+    scene.close()
+
+
+def test_bad_calls_raise():
+    import torch
+    d = hs.small_static()
+    scene = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
+    iq = torch.zeros((1, 4, 512), dtype=torch.complex64, device="cuda")
+    with pytest.raises(harm.HarmError):
+        harm.harm_echo_accumulate(scene, 62, 4, iq)  # beyond the burst
+    with pytest.raises(harm.HarmError):
+        harm.harm_echo_accumulate(scene, 0, 4, iq.cpu())
+    with pytest.raises(harm.HarmError):
+        harm.harm_echo_accumulate(scene, 0, 4, torch.zeros((1, 4, 512), device="cuda"))
+    with pytest.raises(harm.HarmError):
+        harm.harm_echo_adjoint(scene, 0, 4, iq)  # no cells set
+    scene.close()
+
+
+def test_repeat_runs_agree():
+    d = small_wave_scene(n_pulses=32)
+    a = run_echo(d, harm.HARM_PREC_MIXED, 0, 32, "c64")
+    b = run_echo(d, harm.HARM_PREC_MIXED, 0, 32, "c64")
+    assert rel_rms(a, b) < 1e-6
