@@ -15,10 +15,12 @@
 //     Taylor coefficients eta_m = Re sum_w Q_w E_{w,m} accumulated over the wave
 //     components (register-blocked FP32 contraction, separable phasors Q).
 //  3. For each pulse: Horner gives (eta, eta_x, eta_y); each facet forms its
-//     contribution for every channel (Eq. 3, 4, 16), spreads it over 8 bins with
-//     the Kaiser-sinc taps (polynomials in the fractional bin) and the warp
-//     pre-reduces the 32 lanes' taps through a shared-memory transpose into a
-//     16-bin window; the window is added to the CTA's range tile; the tile is
+//     contribution for every channel (Eq. 3, 4, 16) and its 8 Kaiser-sinc taps
+//     (polynomials in the fractional bin). The warp pre-reduces its 32 lanes'
+//     taps: each lane writes its taps into its own column of a per-warp
+//     [16 bin x 32 lane] shared buffer at the rows of its bins, then each lane
+//     sums one bin-row half with vector loads; one shared atomic per
+//     (bin, component) adds the warp's window to the CTA range tile, which is
 //     flushed to the IQ with one vector atomic per bin and channel.
 #include <cuda_runtime.h>
 
@@ -39,28 +41,28 @@ constexpr int WT = 48;        // range bins per channel in the CTA tile
 constexpr int WT_LO = 22;     // tile window starts WT_LO bins below the reference bin
 constexpr int NBMAX = 32;     // pulses per batch
 constexpr int WCH = 128;      // wave components per shared-memory chunk
-constexpr int STG = 20;       // staging row stride (floats) of the warp transpose
+constexpr int SROW = 72;      // floats per bin row of the warp buffer (2 halves of 32 + pad)
+constexpr int SHALF = 36;     // float offset of lanes 16..31 in a row
+constexpr int SBINS = 16;     // bins per warp window
 constexpr float kPiF = 3.14159265358979f;
 
-struct TxRec {
-    float u[3];
-    float invR, inv2R, inv2R2;
-    float u0, v0;
-    float aR[3], eR[3];
-    float ampr;
+// FP32 tile reference of one antenna for one pulse (16 floats).
+struct __align__(16) AntRec {
+    float ux, uy, uz, invR;      // unit vector to the tile reference point, 1/R
+    float inv2R, inv2R2, u0, v0; // 1/(2R), 1/(2R^2), pattern direction cosines
+    float aRx, aRy, aRz, ampr;   // azimuth axis / R, Rbar / R
+    float eRx, eRy, eRz, pad;    // elevation axis / R
 };
 
-struct RxRec {
-    float u[3];
-    float invR, inv2R, inv2R2;
-    float u0, v0;
-    float aR[3], eR[3];
-    float ampr;
-    float psi, ax, ay, gam, pfrac;
-    int kbase;
+// Per (pulse, channel) phase and range references of the tile.
+struct __align__(16) ChanRec {
+    float psi, ax, ay, gam;  // reduced reference phase, lattice phase steps, vertical phase rate
+    float pfrac;             // fractional bin of the reference point
+    int kbase;               // integer bin of the reference point
+    float pad0, pad1;
 };
 
-struct PulseRec {
+struct __align__(16) PulseRec {
     float tau, k0t;
     int epoch;
     int pad;
@@ -71,24 +73,74 @@ struct MixedArgs {
     const float2 *ex, *ey, *wt;
     const float *tau;
     int nb, n_batches;
+    // FP32 constants
+    float tx_laz_l, tx_lel_l;  // aperture / wavelength
+    float rx_laz_l[kMaxCh], rx_lel_l[kMaxCh];
+    float wcos, wsin, wind_mod, area, k0, inv_dr;
     float tap[8][kTapDeg + 1];
+    float sinc2[kSincDeg + 1];
 };
+
+// Shared-memory layout (bytes), sized for nc channels.
+struct Layout {
+    int w, tile, tx, rx, ch, pr, txd, stage, total;
+};
+
+__host__ __device__ inline Layout layout(int nc)
+{
+    Layout L;
+    int o = 0;
+    L.w = o;     o += WCH * 3 * kOrders * 8;
+    L.tile = o;  o += 2 * nc * WT * 8;
+    L.tx = o;    o += NBMAX * (int)sizeof(AntRec);
+    L.rx = o;    o += NBMAX * nc * (int)sizeof(AntRec);
+    L.ch = o;    o += NBMAX * nc * (int)sizeof(ChanRec);
+    L.pr = o;    o += NBMAX * (int)sizeof(PulseRec);
+    L.txd = o;   o += NBMAX * 4 * 8;
+    L.stage = o; o += NWARP * SBINS * SROW * 4;
+    L.total = o;
+    return L;
+}
 
 struct Smem {
-    float2 w[WCH][3][kOrders];          // Taylor tables chunk
-    float2 tile[2][kMaxCh][WT];         // double-buffered range tiles
-    TxRec tx[NBMAX];
-    RxRec rx[NBMAX][kMaxCh];
-    PulseRec pr[NBMAX];
-    double txd[NBMAX][4];               // FP64 tx unit vector + tile offset
-    float stage[NWARP][32 * STG];       // warp transpose staging
+    float2 *w;       // [WCH][3][kOrders]
+    float2 *tile;    // [2][nc][WT]
+    AntRec *tx;      // [NBMAX]
+    AntRec *rx;      // [NBMAX][nc]
+    ChanRec *ch;     // [NBMAX][nc]
+    PulseRec *pr;    // [NBMAX]
+    double *txd;     // [NBMAX][4]
+    float *stage;    // [NWARP][SBINS][SROW]
 };
 
-__device__ __forceinline__ float sinc2f(float x)
+__device__ __forceinline__ Smem carve(unsigned char *raw, int nc)
 {
-    float px = kPiF * x;
-    if (fabsf(px) < 1e-4f) return 1.0f - px * px * (1.0f / 3.0f);
-    float s = __fdividef(sinpif(x), px);
+    Layout L = layout(nc);
+    Smem s;
+    s.w = reinterpret_cast<float2 *>(raw + L.w);
+    s.tile = reinterpret_cast<float2 *>(raw + L.tile);
+    s.tx = reinterpret_cast<AntRec *>(raw + L.tx);
+    s.rx = reinterpret_cast<AntRec *>(raw + L.rx);
+    s.ch = reinterpret_cast<ChanRec *>(raw + L.ch);
+    s.pr = reinterpret_cast<PulseRec *>(raw + L.pr);
+    s.txd = reinterpret_cast<double *>(raw + L.txd);
+    s.stage = reinterpret_cast<float *>(raw + L.stage);
+    return s;
+}
+
+// sinc^2(x): polynomial for |x| <= 1 (main lobe and the start of the first
+// sidelobe), sin(pi x) / (pi x) otherwise.
+__device__ __forceinline__ float sinc2f(const MixedArgs &A, float x)
+{
+    float u = x * x;
+    if (u <= 1.0f) {
+        float t = fmaf(2.0f, u, -1.0f);
+        float r = A.sinc2[kSincDeg];
+#pragma unroll
+        for (int d = kSincDeg - 1; d >= 0; --d) r = fmaf(r, t, A.sinc2[d]);
+        return r;
+    }
+    float s = __fdividef(sinpif(x), kPiF * x);
     return s * s;
 }
 
@@ -106,79 +158,84 @@ __device__ __forceinline__ float reduce_phase(float a)
     return a;
 }
 
-// FP64 tile reference of one antenna at position p with frame (a, e) for the
-// tile reference point X = (xr, yr, 0): D = X - p, R = |D|, u = D / R, and the
-// stable offset R - |p| = (|X|^2 - 2 p.X) / (R + |p|).
-__device__ void tile_ref(const AntState &A, double xr, double yr, double laz_unused, double &R, double u[3],
-                         double &dref, float *uf, float &invR, float &inv2R, float &inv2R2, float &u0, float &v0,
-                         float *aR, float *eR, float &ampr)
+// FP64 tile reference of one antenna (state A) for the tile reference point
+// X = (xr, yr, 0): D = X - p, R = |D|, u = D / R, and the stable offset
+// R - |p| = (|X|^2 - 2 p.X) / (R + |p|).
+__device__ void tile_ref(const AntState &A, double xr, double yr, double u[3], double &dref, AntRec &o)
 {
-    (void)laz_unused;
     double D[3] = {xr - A.p[0], yr - A.p[1], -A.p[2]};
-    R = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+    double R = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
     double iR = 1.0 / R;
     for (int i = 0; i < 3; ++i) u[i] = D[i] * iR;
     double xx = xr * xr + yr * yr;
     dref = (xx - 2.0 * (A.p[0] * xr + A.p[1] * yr)) / (R + A.rref);
-    for (int i = 0; i < 3; ++i) {
-        uf[i] = (float)u[i];
-        aR[i] = (float)(A.a[i] * iR);
-        eR[i] = (float)(A.e[i] * iR);
-    }
-    invR = (float)iR;
-    inv2R = (float)(0.5 * iR);
-    inv2R2 = (float)(0.5 * iR * iR);
-    u0 = (float)(u[0] * A.a[0] + u[1] * A.a[1] + u[2] * A.a[2]);
-    v0 = (float)(u[0] * A.e[0] + u[1] * A.e[1] + u[2] * A.e[2]);
-    ampr = (float)(A.rref * iR);
+    o.ux = (float)u[0];
+    o.uy = (float)u[1];
+    o.uz = (float)u[2];
+    o.invR = (float)iR;
+    o.inv2R = (float)(0.5 * iR);
+    o.inv2R2 = (float)(0.5 * iR * iR);
+    o.u0 = (float)(u[0] * A.a[0] + u[1] * A.a[1] + u[2] * A.a[2]);
+    o.v0 = (float)(u[0] * A.e[0] + u[1] * A.e[1] + u[2] * A.e[2]);
+    o.aRx = (float)(A.a[0] * iR);
+    o.aRy = (float)(A.a[1] * iR);
+    o.aRz = (float)(A.a[2] * iR);
+    o.ampr = (float)(A.rref * iR);
+    o.eRx = (float)(A.e[0] * iR);
+    o.eRy = (float)(A.e[1] * iR);
+    o.eRz = (float)(A.e[2] * iR);
+    o.pad = 0.0f;
 }
 
-// FP64 references of the batch's pulses [pa, pe) for the tile with reference
-// point (xr, yr); thread-parallel over (pulse, antenna). Needs a barrier between
-// the transmit and receive stages.
-__device__ void build_refs(Smem &sm, const MixedArgs &A, int pa, int pe, double xr, double yr)
+// FP64 references of the batch's pulses [pa, pe) for the tile reference point
+// (xr, yr); thread-parallel over (pulse, antenna), one barrier between the
+// transmit and receive stages.
+__device__ void build_refs(const Smem &sm, const MixedArgs &A, int pa, int pe, double xr, double yr)
 {
     const DevScene &S = A.S;
     const int npb = pe - pa;
     for (int t = threadIdx.x; t < npb; t += NT) {
         int n = pa + t;
         const PulseState &P = S.pulses[n];
-        TxRec &T = sm.tx[t];
-        double R, u[3], dref;
-        tile_ref(P.tx, xr, yr, 0.0, R, u, dref, T.u, T.invR, T.inv2R, T.inv2R2, T.u0, T.v0, T.aR, T.eR, T.ampr);
-        sm.txd[t][0] = u[0];
-        sm.txd[t][1] = u[1];
-        sm.txd[t][2] = u[2];
-        sm.txd[t][3] = dref;
-        PulseRec &pr = sm.pr[t];
+        double u[3], dref;
+        tile_ref(P.tx, xr, yr, u, dref, sm.tx[t]);
+        sm.txd[4 * t + 0] = u[0];
+        sm.txd[4 * t + 1] = u[1];
+        sm.txd[4 * t + 2] = u[2];
+        sm.txd[4 * t + 3] = dref;
+        PulseRec pr;
         pr.tau = A.tau[n];
         pr.k0t = (float)(S.k0 * P.t);
         pr.epoch = S.epoch_pulses > 0 ? n / S.epoch_pulses : 0;
+        pr.pad = 0;
+        sm.pr[t] = pr;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < npb * S.nc; t += NT) {
         int pi = t / S.nc, c = t % S.nc;
         int n = pa + pi;
         const RxState &Rs = S.rx[(size_t)n * S.nc + c];
-        RxRec &Q = sm.rx[pi][c];
-        double R, u[3], dref;
-        tile_ref(Rs.rx, xr, yr, 0.0, R, u, dref, Q.u, Q.invR, Q.inv2R, Q.inv2R2, Q.u0, Q.v0, Q.aR, Q.eR, Q.ampr);
-        double off = sm.txd[pi][3] + dref;  // (R_t + R_r) - (Rbar_t + Rbar_r)
-        Q.psi = (float)wrap_pi(Rs.psi - S.k0 * off);
-        double sx = sm.txd[pi][0] + u[0], sy = sm.txd[pi][1] + u[1], sz = sm.txd[pi][2] + u[2];
-        Q.ax = (float)wrap_pi(-S.k0 * sx * S.dx);
-        Q.ay = (float)wrap_pi(-S.k0 * sy * S.dx);
-        Q.gam = (float)(-S.k0 * sz);
+        double u[3], dref;
+        tile_ref(Rs.rx, xr, yr, u, dref, sm.rx[t]);
+        const double *td = sm.txd + 4 * pi;
+        double off = td[3] + dref;  // (R_t + R_r) - (Rbar_t + Rbar_r)
+        ChanRec q;
+        q.psi = (float)wrap_pi(Rs.psi - S.k0 * off);
+        q.ax = (float)wrap_pi(-S.k0 * (td[0] + u[0]) * S.dx);
+        q.ay = (float)wrap_pi(-S.k0 * (td[1] + u[1]) * S.dx);
+        q.gam = (float)(-S.k0 * (td[2] + u[2]));
         double p = Rs.p_ref + off * S.inv_dr;
         double kb = floor(p);
-        Q.kbase = (int)kb;
-        Q.pfrac = (float)(p - kb);
+        q.kbase = (int)kb;
+        q.pfrac = (float)(p - kb);
+        q.pad0 = q.pad1 = 0.0f;
+        sm.ch[t] = q;
     }
 }
 
 // Taylor coefficients of (eta, eta_x, eta_y) in time for two facets (column ix,
 // rows iya / iyb), accumulated over the wave components in shared-memory chunks.
-__device__ void taylor_coeffs(Smem &sm, const MixedArgs &A, int batch, int ix, int iya, int iyb, bool va, bool vb,
+__device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int ix, int iya, int iyb,
                               float ca[3][kOrders], float cb[3][kOrders])
 {
     const DevScene &S = A.S;
@@ -192,8 +249,7 @@ __device__ void taylor_coeffs(Smem &sm, const MixedArgs &A, int batch, int ix, i
         const int cnt = min(WCH, nw - m0);
         __syncthreads();
         const float2 *src = A.wt + ((size_t)batch * nw + m0) * 3 * kOrders;
-        float2 *dst = &sm.w[0][0][0];
-        for (int i = threadIdx.x; i < cnt * 3 * kOrders; i += NT) dst[i] = src[i];
+        for (int i = threadIdx.x; i < cnt * 3 * kOrders; i += NT) sm.w[i] = src[i];
         __syncthreads();
         for (int m = 0; m < cnt; ++m) {
             float2 e = __ldg(A.ex + (size_t)(m0 + m) * S.nx + ixc);
@@ -201,21 +257,20 @@ __device__ void taylor_coeffs(Smem &sm, const MixedArgs &A, int batch, int ix, i
             float2 yb = __ldg(A.ey + (size_t)(m0 + m) * S.ny + iybc);
             float qar = e.x * ya.x - e.y * ya.y, qai = e.x * ya.y + e.y * ya.x;
             float qbr = e.x * yb.x - e.y * yb.y, qbi = e.x * yb.y + e.y * yb.x;
+            const float2 *wm = sm.w + m * 3 * kOrders;
 #pragma unroll
             for (int f = 0; f < 3; ++f)
 #pragma unroll
                 for (int o = 0; o < kOrders; ++o) {
-                    float2 w = sm.w[m][f][o];
+                    float2 w = wm[f * kOrders + o];
                     ca[f][o] = fmaf(qar, w.x, fmaf(-qai, w.y, ca[f][o]));
                     cb[f][o] = fmaf(qbr, w.x, fmaf(-qbi, w.y, cb[f][o]));
                 }
         }
     }
-    (void)va;
-    (void)vb;
 }
 
-__device__ __forceinline__ float horner5(const float c[kOrders], float t)
+__device__ __forceinline__ float horner(const float c[kOrders], float t)
 {
     float r = c[kOrders - 1];
 #pragma unroll
@@ -256,43 +311,56 @@ __device__ __forceinline__ void gadd1(OutT *iq, size_t idx, int comp, float v)
 }
 
 // Warp pre-reduction of the lanes' 8 complex taps at bins kb .. kb + 7 into a
-// 16-bin window through a shared-memory transpose, then one shared atomic per
-// (bin, component) into the CTA range tile (or a global atomic outside it).
+// 16-bin window. Each lane writes its taps into its own column of the warp
+// buffer (rows = bins relative to the warp's lowest bin; the buffer is all
+// zero between calls), then lane (w, half) sums half of bin row w with vector
+// loads, the halves combine by one shuffle, and one shared atomic per
+// (bin, component) adds the window to the CTA range tile (a global atomic
+// outside it). Lanes whose bins spread over more than 8 bins fall back to
+// direct atomics.
 template <typename OutT>
-__device__ __forceinline__ void warp_scatter(float *stage, float2 *tile_c, int tile_base, int kb, bool valid,
+__device__ __forceinline__ void warp_scatter(float *buf, float2 *tile_c, int tile_base, int kb, bool valid,
                                              const float h[8], float sr, float si, int nr, OutT *grow,
                                              unsigned int *flags)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    int kmin = __reduce_min_sync(FULL, valid ? kb : INT_MAX);
+    const int kmin = __reduce_min_sync(FULL, valid ? kb : INT_MAX);
     if (kmin == INT_MAX) return;
-    int kmax = __reduce_max_sync(FULL, valid ? kb : INT_MIN);
-    if (kmax - kmin <= 8) {
-        int o = valid ? kb - kmin : 0;
-        float4 *row = reinterpret_cast<float4 *>(stage + lane * STG);
-        float a = valid ? sr : 0.0f, b = valid ? si : 0.0f;
-        row[0] = make_float4(h[0] * a, h[0] * b, h[1] * a, h[1] * b);
-        row[1] = make_float4(h[2] * a, h[2] * b, h[3] * a, h[3] * b);
-        row[2] = make_float4(h[4] * a, h[4] * b, h[5] * a, h[5] * b);
-        row[3] = make_float4(h[6] * a, h[6] * b, h[7] * a, h[7] * b);
-        __syncwarp();
-        const int w = lane >> 1, comp = lane & 1;
-        float acc = 0.0f;
-#pragma unroll 8
-        for (int src = 0; src < 32; ++src) {
-            int os = __shfl_sync(FULL, o, src);
-            int j = w - os;
-            if ((unsigned)j < 8u) acc += stage[src * STG + 2 * j + comp];
+    const int kmax = __reduce_max_sync(FULL, valid ? kb : INT_MIN);
+    if (kmax - kmin <= SBINS - 8) {
+        float *col = buf + (lane < 16 ? 2 * lane : SHALF + 2 * (lane - 16));
+        const int o = kb - kmin;
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<float2 *>(col + (o + j) * SROW) = make_float2(h[j] * sr, h[j] * si);
         }
         __syncwarp();
-        int k = kmin + w;
-        if (acc != 0.0f && k >= 0 && k < nr) {
-            int tw = k - tile_base;
+        const int w = lane >> 1, half = lane & 1;
+        const float4 *rp = reinterpret_cast<const float4 *>(buf + w * SROW + half * SHALF);
+        float ar = 0.0f, ai = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float4 v = rp[q];
+            ar += v.x + v.z;
+            ai += v.y + v.w;
+        }
+        ar += __shfl_xor_sync(FULL, ar, 1);
+        ai += __shfl_xor_sync(FULL, ai, 1);
+        __syncwarp();
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) *reinterpret_cast<float2 *>(col + (o + j) * SROW) = make_float2(0.f, 0.f);
+        }
+        const float val = half ? ai : ar;
+        const int k = kmin + w;
+        if (val != 0.0f && k >= 0 && k < nr) {
+            const int tw = k - tile_base;
             if (tw >= 0 && tw < WT) {
-                atomicAdd(reinterpret_cast<float *>(tile_c + tw) + comp, acc);
+                atomicAdd(reinterpret_cast<float *>(tile_c + tw) + half, val);
             } else {
-                gadd1<OutT>(grow, (size_t)k, comp, acc);
+                gadd1<OutT>(grow, (size_t)k, half, val);
                 atomicAdd(flags + 2, 1u);
             }
         }
@@ -314,93 +382,94 @@ __device__ __forceinline__ void warp_scatter(float *stage, float2 *tile_c, int t
 }
 
 struct FacetGeo {
-    float xi_y;     // y offset from the tile reference point (exact)
-    int jrow;       // row offset index
+    float xi_y;          // y offset from the tile reference point (exact)
+    float fj;            // row offset index
     float base, cu, cv;  // NRCS base and current (cell values or uniform)
-    float2 z;       // speckle of the current epoch
-    int epoch;      // epoch the speckle belongs to
+    float2 z;            // speckle of the current epoch
+    int epoch;           // epoch the speckle belongs to
     uint32_t fid;
     bool valid;
 };
 
 template <int TAPS, typename OutT>
-__device__ __forceinline__ void facet_pulse(Smem &sm, const MixedArgs &A, const FacetGeo &G, const float c[3][kOrders],
-                                            int pi, int n, int n0, int np, int buf, float xi_x, float fi, float *stage,
-                                            OutT *iq)
+__device__ __forceinline__ void facet_pulse(const Smem &sm, const MixedArgs &A, const FacetGeo &G,
+                                            const float c[3][kOrders], int pi, int n, int n0, int np, int buf,
+                                            float xi_x, float fi, float *stage, OutT *iq)
 {
     const DevScene &S = A.S;
-    const PulseRec &PR = sm.pr[pi];
-    const float tau = PR.tau;
-    const float eta = horner5(c[0], tau);
-    const float sx = horner5(c[1], tau);
-    const float sy = horner5(c[2], tau);
-    const float xi[3] = {xi_x, G.xi_y, eta};
-    const float b2 = fmaf(xi[0], xi[0], fmaf(xi[1], xi[1], eta * eta));
+    const int nc = S.nc;
+    const PulseRec PR = sm.pr[pi];
+    const float eta = horner(c[0], PR.tau);
+    const float sx = horner(c[1], PR.tau);
+    const float sy = horner(c[2], PR.tau);
+    const float xi0 = xi_x, xi1 = G.xi_y, xi2 = eta;
+    const float b2 = fmaf(xi0, xi0, fmaf(xi1, xi1, eta * eta));
     const float inv_n = rsqrtf(fmaf(sx, sx, fmaf(sy, sy, 1.0f)));
-    const float fj = (float)G.jrow;
 
     // transmit leg (shared by the channels)
-    const TxRec &T = sm.tx[pi];
-    const float at = fmaf(T.u[0], xi[0], fmaf(T.u[1], xi[1], T.u[2] * xi[2]));
+    const AntRec T = sm.tx[pi];
+    const float at = fmaf(T.ux, xi0, fmaf(T.uy, xi1, T.uz * xi2));
     const float st = fmaf(-at, at, b2);
     const float qt = st * fmaf(-at, T.inv2R2, T.inv2R);
     const float dt = at + qt;
     const float et = dt * T.invR;
     const float rho_t = fmaf(et, et, 1.0f - et);
-    const float ut = (T.u0 + fmaf(xi[0], T.aR[0], fmaf(xi[1], T.aR[1], xi[2] * T.aR[2]))) * rho_t;
-    const float vt = (T.v0 + fmaf(xi[0], T.eR[0], fmaf(xi[1], T.eR[1], xi[2] * T.eR[2]))) * rho_t;
-    const float inv_lam = (float)S.inv_lambda;
-    const float gt = sinc2f((float)S.tx_laz * inv_lam * ut) * sinc2f((float)S.tx_lel * inv_lam * vt);
-    const float rt[3] = {fmaf(xi[0], T.invR, T.u[0]) * rho_t, fmaf(xi[1], T.invR, T.u[1]) * rho_t,
-                         fmaf(xi[2], T.invR, T.u[2]) * rho_t};
+    const float ut = (T.u0 + fmaf(xi0, T.aRx, fmaf(xi1, T.aRy, xi2 * T.aRz))) * rho_t;
+    const float vt = (T.v0 + fmaf(xi0, T.eRx, fmaf(xi1, T.eRy, xi2 * T.eRz))) * rho_t;
+    const float gt = sinc2f(A, A.tx_laz_l * ut) * sinc2f(A, A.tx_lel_l * vt);
+    const float rt0 = fmaf(xi0, T.invR, T.ux) * rho_t;
+    const float rt1 = fmaf(xi1, T.invR, T.uy) * rho_t;
+    const float rt2 = fmaf(xi2, T.invR, T.uz) * rho_t;
     const float ampt = gt * T.ampr * rho_t;
-    const float k0f = (float)S.k0;
-    const float inv_dr = (float)S.inv_dr;
 
-    for (int ch = 0; ch < S.nc; ++ch) {
-        const RxRec &R = sm.rx[pi][ch];
-        const float ar = fmaf(R.u[0], xi[0], fmaf(R.u[1], xi[1], R.u[2] * xi[2]));
+    const AntRec *RX = sm.rx + pi * nc;
+    const ChanRec *CH = sm.ch + pi * nc;
+    for (int ch = 0; ch < nc; ++ch) {
+        const AntRec R = RX[ch];
+        const ChanRec Q = CH[ch];
+        const float ar = fmaf(R.ux, xi0, fmaf(R.uy, xi1, R.uz * xi2));
         const float sr_ = fmaf(-ar, ar, b2);
         const float qr = sr_ * fmaf(-ar, R.inv2R2, R.inv2R);
         const float dr = ar + qr;
         const float er = dr * R.invR;
         const float rho_r = fmaf(er, er, 1.0f - er);
-        const float ur = (R.u0 + fmaf(xi[0], R.aR[0], fmaf(xi[1], R.aR[1], xi[2] * R.aR[2]))) * rho_r;
-        const float vr = (R.v0 + fmaf(xi[0], R.eR[0], fmaf(xi[1], R.eR[1], xi[2] * R.eR[2]))) * rho_r;
-        const float gr = sinc2f((float)S.rx_laz[ch] * inv_lam * ur) * sinc2f((float)S.rx_lel[ch] * inv_lam * vr);
-        const float qx = -(rt[0] + fmaf(xi[0], R.invR, R.u[0]) * rho_r);
-        const float qy = -(rt[1] + fmaf(xi[1], R.invR, R.u[1]) * rho_r);
-        const float qz = -(rt[2] + fmaf(xi[2], R.invR, R.u[2]) * rho_r);
+        const float ur = (R.u0 + fmaf(xi0, R.aRx, fmaf(xi1, R.aRy, xi2 * R.aRz))) * rho_r;
+        const float vr = (R.v0 + fmaf(xi0, R.eRx, fmaf(xi1, R.eRy, xi2 * R.eRz))) * rho_r;
+        const float gr = sinc2f(A, A.rx_laz_l[ch] * ur) * sinc2f(A, A.rx_lel_l[ch] * vr);
+        const float qx = -fmaf(fmaf(xi0, R.invR, R.ux), rho_r, rt0);
+        const float qy = -fmaf(fmaf(xi1, R.invR, R.uy), rho_r, rt1);
+        const float qz = -fmaf(fmaf(xi2, R.invR, R.uz), rho_r, rt2);
         float sig = G.base;
         if (!S.static_surface) {
             float qh2 = fmaf(qx, qx, qy * qy);
-            float cphi = qh2 > 0.0f ? fmaf((float)S.wcos, qx, (float)S.wsin * qy) * rsqrtf(qh2) : 0.0f;
+            float cphi = qh2 > 0.0f ? fmaf(A.wcos, qx, A.wsin * qy) * rsqrtf(qh2) : 0.0f;
             float nq = fmaf(-sx, qx, fmaf(-sy, qy, qz));
             float tilt = __fdividef(fmaxf(nq, 0.0f) * inv_n, qz);
-            sig = G.base * fmaf((float)S.wind_mod, cphi, 1.0f) * tilt;
+            sig = G.base * fmaf(A.wind_mod, cphi, 1.0f) * tilt;
         }
-        const float amp = sqrtf(sig * (float)S.area) * ampt * gr * R.ampr * rho_r;
+        const float sa = sig * A.area;
+        const float amp = (sa > 0.0f ? sa * rsqrtf(sa) : 0.0f) * ampt * gr * R.ampr * rho_r;
         const float vc = -fmaf(G.cu, qx, G.cv * qy);
-        float phi = R.psi + fmaf(fi, R.ax, fmaf(fj, R.ay, fmaf(R.gam, eta, -k0f * (qt + qr))));
+        float phi = Q.psi + fmaf(fi, Q.ax, fmaf(G.fj, Q.ay, fmaf(Q.gam, eta, -A.k0 * (qt + qr))));
         phi = fmaf(-PR.k0t, vc, phi);
         phi = reduce_phase(phi);
         float sp, cp;
         __sincosf(phi, &sp, &cp);
         const float zr = amp * G.z.x, zi = amp * G.z.y;
-        const float vr_ = zr * cp - zi * sp;
-        const float vi_ = fmaf(zr, sp, zi * cp);
-        const float p = fmaf(dt + dr, inv_dr, R.pfrac);
+        const float vre = zr * cp - zi * sp;
+        const float vim = fmaf(zr, sp, zi * cp);
+        const float p = fmaf(dt + dr, A.inv_dr, Q.pfrac);
         const float kf = floorf(p);
         const float fr = p - kf;
         int kb;
         float h[8];
         if (TAPS == 1) {
-            kb = R.kbase + (int)kf;
+            kb = Q.kbase + (int)kf;
             h[0] = 1.0f;
 #pragma unroll
             for (int j = 1; j < 8; ++j) h[j] = 0.0f;
         } else {
-            kb = R.kbase + (int)kf - 3;
+            kb = Q.kbase + (int)kf - 3;
             const float t = fmaf(2.0f, fr, -1.0f);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -410,10 +479,10 @@ __device__ __forceinline__ void facet_pulse(Smem &sm, const MixedArgs &A, const 
                 h[j] = v;
             }
         }
-        float2 *tile_c = sm.tile[buf][ch];
-        const int tile_base = R.kbase - WT_LO;
+        float2 *tile_c = sm.tile + (buf * nc + ch) * WT;
+        const int tile_base = Q.kbase - WT_LO;
         OutT *grow = iq + 2 * ((size_t)ch * np + (n - n0)) * S.nr;
-        warp_scatter<OutT>(stage, tile_c, tile_base, kb, G.valid, h, vr_, vi_, S.nr, grow, S.flags);
+        warp_scatter<OutT>(stage, tile_c, tile_base, kb, G.valid, h, vre, vim, S.nr, grow, S.flags);
     }
 }
 
@@ -421,8 +490,8 @@ __device__ void facet_setup(const MixedArgs &A, int ix, int iy, int jref, FacetG
 {
     const DevScene &S = A.S;
     G.valid = ix < S.nx && iy < S.ny;
-    G.jrow = iy - jref;
-    G.xi_y = (float)(G.jrow * S.dx);
+    G.fj = (float)(iy - jref);
+    G.xi_y = (float)((iy - jref) * S.dx);
     G.fid = (uint32_t)min(iy, S.ny - 1) * (uint32_t)S.nx + (uint32_t)min(ix, S.nx - 1);
     double base = S.sigma0_base, cu = S.cur_u, cv = S.cur_v;
     if (S.cell_sigma0 || S.cell_uv) {
@@ -443,14 +512,16 @@ __device__ void facet_setup(const MixedArgs &A, int ix, int iy, int jref, FacetG
     G.cu = (float)cu;
     G.cv = (float)cv;
     G.epoch = -1;
+    G.z = make_float2(0.f, 0.f);
 }
 
 template <int TAPS, typename OutT>
 __global__ void __launch_bounds__(NT, 2) accumulate_mixed_kernel(MixedArgs A, int n0, int np, int b0, OutT *iq)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const DevScene &S = A.S;
+    const int nc = S.nc;
+    const Smem sm = carve(smem_raw, nc);
     const int tiles_x = (S.nx + TX - 1) / TX;
     const int tx0 = (blockIdx.x % tiles_x) * TX;
     const int ty0 = (blockIdx.x / tiles_x) * TY;
@@ -466,7 +537,8 @@ __global__ void __launch_bounds__(NT, 2) accumulate_mixed_kernel(MixedArgs A, in
     const float xi_x = (float)((ix - iref) * S.dx);
     const float fi = (float)(ix - iref);
 
-    for (int i = threadIdx.x; i < 2 * kMaxCh * WT; i += NT) (&sm.tile[0][0][0])[i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < 2 * nc * WT; i += NT) sm.tile[i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < NWARP * SBINS * SROW; i += NT) sm.stage[i] = 0.0f;
     build_refs(sm, A, pa, pe, xr, yr);
 
     FacetGeo ga, gb;
@@ -474,7 +546,7 @@ __global__ void __launch_bounds__(NT, 2) accumulate_mixed_kernel(MixedArgs A, in
     facet_setup(A, ix, ty0 + warp + NWARP, jref, gb);
     float ca[3][kOrders], cb[3][kOrders];
     if (!S.static_surface && S.nw > 0) {
-        taylor_coeffs(sm, A, batch, ix, ty0 + warp, ty0 + warp + NWARP, ga.valid, gb.valid, ca, cb);
+        taylor_coeffs(sm, A, batch, ix, ty0 + warp, ty0 + warp + NWARP, ca, cb);
     } else {
 #pragma unroll
         for (int f = 0; f < 3; ++f)
@@ -483,7 +555,7 @@ __global__ void __launch_bounds__(NT, 2) accumulate_mixed_kernel(MixedArgs A, in
     }
     __syncthreads();
 
-    float *stage = sm.stage[warp];
+    float *stage = sm.stage + warp * SBINS * SROW;
     for (int n = pa; n < pe; ++n) {
         const int pi = n - pa;
         const int buf = pi & 1;
@@ -499,11 +571,12 @@ __global__ void __launch_bounds__(NT, 2) accumulate_mixed_kernel(MixedArgs A, in
         facet_pulse<TAPS, OutT>(sm, A, ga, ca, pi, n, n0, np, buf, xi_x, fi, stage, iq);
         facet_pulse<TAPS, OutT>(sm, A, gb, cb, pi, n, n0, np, buf, xi_x, fi, stage, iq);
         __syncthreads();
-        for (int i = threadIdx.x; i < S.nc * WT; i += NT) {
+        for (int i = threadIdx.x; i < nc * WT; i += NT) {
             int ch = i / WT, w = i % WT;
-            float2 v = sm.tile[buf][ch][w];
-            sm.tile[buf][ch][w] = make_float2(0.f, 0.f);
-            int k = sm.rx[pi][ch].kbase - WT_LO + w;
+            float2 *slot = sm.tile + (buf * nc + ch) * WT + w;
+            float2 v = *slot;
+            *slot = make_float2(0.f, 0.f);
+            int k = sm.ch[pi * nc + ch].kbase - WT_LO + w;
             if ((v.x != 0.0f || v.y != 0.0f) && k >= 0 && k < S.nr)
                 gadd<OutT>(iq + 2 * ((size_t)ch * np + (n - n0)) * S.nr, (size_t)k, v.x, v.y);
         }
@@ -514,8 +587,8 @@ __global__ void __launch_bounds__(NT, 2) accumulate_mixed_kernel(MixedArgs A, in
 __global__ void __launch_bounds__(NT, 2) generate_mixed_kernel(MixedArgs A, int n0, int np, int b0, float *state)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const DevScene &S = A.S;
+    const Smem sm = carve(smem_raw, S.nc);
     const int tiles_x = (S.nx + TX - 1) / TX;
     const int tx0 = (blockIdx.x % tiles_x) * TX;
     const int ty0 = (blockIdx.x / tiles_x) * TY;
@@ -529,7 +602,7 @@ __global__ void __launch_bounds__(NT, 2) generate_mixed_kernel(MixedArgs A, int 
     const bool va = ix < S.nx && iya < S.ny, vb = ix < S.nx && iyb < S.ny;
     float ca[3][kOrders], cb[3][kOrders];
     if (!S.static_surface && S.nw > 0) {
-        taylor_coeffs(sm, A, batch, ix, iya, iyb, va, vb, ca, cb);
+        taylor_coeffs(sm, A, batch, ix, iya, iyb, ca, cb);
     } else {
 #pragma unroll
         for (int f = 0; f < 3; ++f)
@@ -542,15 +615,15 @@ __global__ void __launch_bounds__(NT, 2) generate_mixed_kernel(MixedArgs A, int 
         float *o = state + (size_t)(n - n0) * 3 * nf;
         if (va) {
             int64_t f = (int64_t)iya * S.nx + ix;
-            o[f] = horner5(ca[0], tau);
-            o[nf + f] = horner5(ca[1], tau);
-            o[2 * nf + f] = horner5(ca[2], tau);
+            o[f] = horner(ca[0], tau);
+            o[nf + f] = horner(ca[1], tau);
+            o[2 * nf + f] = horner(ca[2], tau);
         }
         if (vb) {
             int64_t f = (int64_t)iyb * S.nx + ix;
-            o[f] = horner5(cb[0], tau);
-            o[nf + f] = horner5(cb[1], tau);
-            o[2 * nf + f] = horner5(cb[2], tau);
+            o[f] = horner(cb[0], tau);
+            o[nf + f] = horner(cb[1], tau);
+            o[2 * nf + f] = horner(cb[2], tau);
         }
     }
 }
@@ -565,30 +638,46 @@ MixedArgs make_args(const DevScene &S, const MixedTables &M)
     A.tau = M.tau;
     A.nb = M.nb;
     A.n_batches = M.n_batches;
+    A.tx_laz_l = (float)(S.tx_laz * S.inv_lambda);
+    A.tx_lel_l = (float)(S.tx_lel * S.inv_lambda);
+    for (int c = 0; c < kMaxCh; ++c) {
+        A.rx_laz_l[c] = c < S.nc ? (float)(S.rx_laz[c] * S.inv_lambda) : 0.0f;
+        A.rx_lel_l[c] = c < S.nc ? (float)(S.rx_lel[c] * S.inv_lambda) : 0.0f;
+    }
+    A.wcos = (float)S.wcos;
+    A.wsin = (float)S.wsin;
+    A.wind_mod = (float)S.wind_mod;
+    A.area = (float)S.area;
+    A.k0 = (float)S.k0;
+    A.inv_dr = (float)S.inv_dr;
     for (int j = 0; j < 8; ++j)
         for (int d = 0; d <= kTapDeg; ++d) A.tap[j][d] = M.tap[j][d];
+    for (int d = 0; d <= kSincDeg; ++d) A.sinc2[d] = M.sinc2[d];
     return A;
 }
 
 template <typename K>
-cudaError_t set_smem(K kernel)
+cudaError_t prep(K kernel, int bytes)
 {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 }  // namespace
+
+int mixed_smem_bytes(int nc) { return layout(nc).total; }
 
 cudaError_t launch_generate_mixed(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np,
                                   float *state)
 {
     MixedArgs A = make_args(S, M);
-    cudaError_t e = set_smem(generate_mixed_kernel);
+    const int bytes = layout(S.nc).total;
+    cudaError_t e = prep(generate_mixed_kernel, bytes);
     if (e != cudaSuccess) return e;
     int tiles = ((S.nx + TX - 1) / TX) * ((S.ny + TY - 1) / TY);
     int b0 = n0 / M.nb, b1 = (n0 + np - 1) / M.nb;
     for (int bb = b0; bb <= b1; bb += 65535) {
         int cnt = min(65535, b1 - bb + 1);
-        generate_mixed_kernel<<<dim3(tiles, cnt), NT, sizeof(Smem), st>>>(A, n0, np, bb, state);
+        generate_mixed_kernel<<<dim3(tiles, cnt), NT, bytes, st>>>(A, n0, np, bb, state);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -598,6 +687,7 @@ cudaError_t launch_accumulate_mixed(const DevScene &S, const MixedTables &M, cud
                                     void *iq, harm_dtype dtype)
 {
     MixedArgs A = make_args(S, M);
+    const int bytes = layout(S.nc).total;
     int tiles = ((S.nx + TX - 1) / TX) * ((S.ny + TY - 1) / TY);
     int b0 = n0 / M.nb, b1 = (n0 + np - 1) / M.nb;
     cudaError_t e;
@@ -606,19 +696,19 @@ cudaError_t launch_accumulate_mixed(const DevScene &S, const MixedTables &M, cud
         dim3 grid(tiles, cnt);
         if (dtype == HARM_C64) {
             if (S.taps == 1) {
-                if ((e = set_smem(accumulate_mixed_kernel<1, float>)) != cudaSuccess) return e;
-                accumulate_mixed_kernel<1, float><<<grid, NT, sizeof(Smem), st>>>(A, n0, np, bb, (float *)iq);
+                if ((e = prep(accumulate_mixed_kernel<1, float>, bytes)) != cudaSuccess) return e;
+                accumulate_mixed_kernel<1, float><<<grid, NT, bytes, st>>>(A, n0, np, bb, (float *)iq);
             } else {
-                if ((e = set_smem(accumulate_mixed_kernel<8, float>)) != cudaSuccess) return e;
-                accumulate_mixed_kernel<8, float><<<grid, NT, sizeof(Smem), st>>>(A, n0, np, bb, (float *)iq);
+                if ((e = prep(accumulate_mixed_kernel<8, float>, bytes)) != cudaSuccess) return e;
+                accumulate_mixed_kernel<8, float><<<grid, NT, bytes, st>>>(A, n0, np, bb, (float *)iq);
             }
         } else {
             if (S.taps == 1) {
-                if ((e = set_smem(accumulate_mixed_kernel<1, double>)) != cudaSuccess) return e;
-                accumulate_mixed_kernel<1, double><<<grid, NT, sizeof(Smem), st>>>(A, n0, np, bb, (double *)iq);
+                if ((e = prep(accumulate_mixed_kernel<1, double>, bytes)) != cudaSuccess) return e;
+                accumulate_mixed_kernel<1, double><<<grid, NT, bytes, st>>>(A, n0, np, bb, (double *)iq);
             } else {
-                if ((e = set_smem(accumulate_mixed_kernel<8, double>)) != cudaSuccess) return e;
-                accumulate_mixed_kernel<8, double><<<grid, NT, sizeof(Smem), st>>>(A, n0, np, bb, (double *)iq);
+                if ((e = prep(accumulate_mixed_kernel<8, double>, bytes)) != cudaSuccess) return e;
+                accumulate_mixed_kernel<8, double><<<grid, NT, bytes, st>>>(A, n0, np, bb, (double *)iq);
             }
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

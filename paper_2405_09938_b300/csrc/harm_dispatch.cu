@@ -76,6 +76,38 @@ void fit_taps(const DevScene &S, float out[8][kTapDeg + 1])
     }
 }
 
+// sinc^2(x) on |x| <= 1 as a polynomial of degree kSincDeg in t = 2 x^2 - 1
+// (Chebyshev interpolation in t, converted to monomials).
+void fit_sinc2(float out[kSincDeg + 1])
+{
+    const int N = kSincDeg + 1;
+    double fv[N], cheb[N];
+    for (int i = 0; i < N; ++i) {
+        double t = std::cos(kPi * (i + 0.5) / N);
+        double x = std::sqrt(0.5 * (t + 1.0));
+        double s = (x == 0.0) ? 1.0 : std::sin(kPi * x) / (kPi * x);
+        fv[i] = s * s;
+    }
+    for (int k = 0; k < N; ++k) {
+        double acc = 0.0;
+        for (int i = 0; i < N; ++i) acc += fv[i] * std::cos(kPi * k * (i + 0.5) / N);
+        cheb[k] = acc * (k == 0 ? 1.0 : 2.0) / N;
+    }
+    double mono[N] = {0}, tkm1[N] = {0}, tk[N] = {0}, tkp1[N];
+    tkm1[0] = 1.0;
+    tk[1] = 1.0;
+    for (int d = 0; d < N; ++d) mono[d] += cheb[0] * tkm1[d] + cheb[1] * tk[d];
+    for (int k = 2; k < N; ++k) {
+        for (int d = 0; d < N; ++d) tkp1[d] = -tkm1[d] + (d > 0 ? 2.0 * tk[d - 1] : 0.0);
+        for (int d = 0; d < N; ++d) mono[d] += cheb[k] * tkp1[d];
+        for (int d = 0; d < N; ++d) {
+            tkm1[d] = tk[d];
+            tk[d] = tkp1[d];
+        }
+    }
+    for (int d = 0; d < N; ++d) out[d] = (float)mono[d];
+}
+
 }  // namespace
 
 harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps, const std::vector<Wave> &waves)
@@ -125,6 +157,7 @@ harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps,
         }
     }
     fit_taps(s->dev, M.tap);
+    fit_sinc2(M.sinc2);
     if (upload_raw(s, ex, &M.ex) != cudaSuccess || upload_raw(s, ey, &M.ey) != cudaSuccess ||
         upload_raw(s, wt, &M.wt) != cudaSuccess || upload_raw(s, tau, &M.tau) != cudaSuccess)
         return HARM_E_CUDA;

@@ -11,7 +11,8 @@ namespace harm {
 
 // Mixed-precision path tables (FP32 separable waves and the Taylor-in-time
 // tables of each pulse batch, plus the tap polynomials).
-constexpr int kTapDeg = 12;     // degree of each tap polynomial in t = 2f - 1
+constexpr int kTapDeg = 10;     // degree of each tap polynomial in t = 2f - 1
+constexpr int kSincDeg = 7;     // degree of the sinc^2 polynomial in t = 2x^2 - 1, |x| <= 1
 constexpr int kOrders = 5;      // Taylor orders in time: tau^0 .. tau^4
 
 struct MixedTables {
@@ -23,6 +24,7 @@ struct MixedTables {
     const float2 *wt = nullptr;   // [n_batches][nw][3][kOrders] Taylor coefficients
     const float *tau = nullptr;   // [np_total] t_s(n) - t_centre(batch)
     float tap[8][kTapDeg + 1];    // Kaiser-sinc tap h(j - f), j = -3..4, monomials in t
+    float sinc2[kSincDeg + 1];    // sinc^2(x) for |x| <= 1, monomials in t = 2 x^2 - 1
 };
 
 }  // namespace harm
