@@ -110,6 +110,8 @@ def lib():
         L.or_echo.restype = C.c_int
         L.or_contribution.argtypes = [C.POINTER(OrScene), C.c_int, C.c_int, C.c_int64, dp, dp]
         L.or_num_threads.restype = C.c_int
+        L.or_adjoint.argtypes = [C.POINTER(OrScene), C.c_int, C.POINTER(C.c_int), dp, dp, dp]
+        L.or_adjoint.restype = C.c_int
         _lib = L
     return _lib
 
@@ -290,3 +292,26 @@ def echo(desc, pulses, facets=None):
 
 def num_threads():
     return lib().or_num_threads()
+
+
+def adjoint(desc, pulses, resid):
+    """Gradients of L = sum |IQ - target|^2 for the residual resid = IQ - target
+    (complex [n_ch, len(pulses), n_range]) with respect to the per-cell NRCS base
+    and (u, v) current: returns (g_sigma [ncy, ncx], g_uv [ncy, ncx, 2])."""
+    sc = Scene(desc)
+    cells = desc["cells"]
+    ncx, ncy = cells["ncx"], cells["ncy"]
+    pl = np.ascontiguousarray(pulses, dtype=np.int32)
+    r = np.ascontiguousarray(np.stack([resid.real, resid.imag], axis=-1), dtype=np.float64)
+    gs = np.zeros(ncx * ncy)
+    gu = np.zeros(ncx * ncy * 2)
+    rc = lib().or_adjoint(sc.ref, len(pl), pl.ctypes.data_as(C.POINTER(C.c_int)), _dptr(r), _dptr(gs),
+                          _dptr(gu))
+    if rc != 0:
+        raise ValueError("adjoint needs per-cell fields")
+    return gs.reshape(ncy, ncx), gu.reshape(ncy, ncx, 2)
+
+
+def misfit(desc, pulses, target):
+    iq = echo(desc, pulses)
+    return float(np.sum(np.abs(iq - target) ** 2)), iq

@@ -363,8 +363,9 @@ double or_range_start(const or_scene *s, int c)
 
 /* One facet's complex contribution at pulse state g (Eq. 3, 4, 16) and its
    fractional range-bin position p. state = (eta, eta_x, eta_y). */
-static void contribution(const or_scene *s, const or_pulse *g, int n, int c, int64_t f,
-                         const double state[3], double r0, double *sre, double *sim, double *p)
+static void contribution_full(const or_scene *s, const or_pulse *g, int n, int c, int64_t f,
+                              const double state[3], double r0, double *sre, double *sim, double *p,
+                              double *sumx, double *sumy, int *cell)
 {
     double lambda = OR_C / s->f0;
     double k0 = 2.0 * OR_PI / lambda;
@@ -396,11 +397,20 @@ static void contribution(const or_scene *s, const or_pulse *g, int n, int c, int
     or_speckle(s->speckle_seed, (uint64_t)f, e, &zr, &zi);
     double vc = cu * (ut[0] + ur[0]) + cv * (ut[1] + ur[1]);
     double phase = -k0 * (rt + rr + vc * g->t);
+    if (sumx) *sumx = ut[0] + ur[0];
+    if (sumy) *sumy = ut[1] + ur[1];
+    if (cell) *cell = (s->ncx > 0) ? cell_index(s, x, y) : -1;
     double cph = cos(phase), sph = sin(phase);
     double ar = amp * zr, ai = amp * zi;
     *sre = ar * cph - ai * sph;
     *sim = ar * sph + ai * cph;
     *p = (rt + rr - r0) / (OR_C / s->fs);
+}
+
+static void contribution(const or_scene *s, const or_pulse *g, int n, int c, int64_t f,
+                         const double state[3], double r0, double *sre, double *sim, double *p)
+{
+    contribution_full(s, g, n, c, f, state, r0, sre, sim, p, NULL, NULL, NULL);
 }
 
 /* Neumaier compensated add of v into (sum, comp). */
@@ -537,4 +547,93 @@ int or_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* Adjoint of the echo with respect to the per-cell NRCS base and current, for
+   the misfit L = sum |IQ - target|^2 with residual r = IQ - target given as
+   resid[c][i][k][2] for the listed pulses. Chain rule on each contribution s
+   spread with weights h(k - p): with g = sum_k h(k - p) r[k] (the transposed
+   spread, a gather over the same bins),
+     dL/dsigma_cell += Re(conj(g) s) / sigma_cell          (s ~ sqrt(sigma))
+     dL/du_cell     += 2 K0 t_n (r_t + r_r)_x Im(conj(g) s) (phase -K0 v_c t_n)
+     dL/dv_cell     += 2 K0 t_n (r_t + r_r)_y Im(conj(g) s)
+   (Eq. 3 and Eq. 4). The current does not move range bins, so h does not
+   depend on it. Gradients are added into g_sigma[ncells] / g_uv[ncells][2]. */
+int or_adjoint(const or_scene *s, int n_list, const int *pulses, const double *resid, double *g_sigma,
+               double *g_uv)
+{
+    if (s->ncx <= 0 || s->ncy <= 0) return -1;
+    int nc = s->n_channels, nr = s->n_range;
+    int64_t nf = (int64_t)s->nx * s->ny;
+    int ncell = s->ncx * s->ncy;
+    int nw = (s->static_surface ? 0 : s->n_omega * s->n_theta);
+    double *kx = NULL, *ky = NULL, *om = NULL, *amp = NULL, *ph = NULL;
+    if (nw > 0) {
+        kx = malloc(sizeof(double) * nw); ky = malloc(sizeof(double) * nw);
+        om = malloc(sizeof(double) * nw); amp = malloc(sizeof(double) * nw);
+        ph = malloc(sizeof(double) * nw);
+        or_wave_table(s, kx, ky, om, amp, ph);
+    }
+    double lambda = OR_C / s->f0;
+    double k0 = 2.0 * OR_PI / lambda;
+    double *st = malloc(sizeof(double) * 3 * nf);
+    double r0[OR_MAXC];
+    for (int c = 0; c < nc; ++c) r0[c] = or_range_start(s, c);
+    /* per-channel partial gradients, summed in channel order at the end */
+    double *part = calloc((size_t)nc * ncell * 3, sizeof(double));
+    for (int i = 0; i < n_list; ++i) {
+        int n = pulses[i];
+        or_facet_states(s, n, nw, kx, ky, om, amp, ph, st);
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int c = 0; c < nc; ++c) {
+            or_pulse g;
+            or_pulse_state(s, n, c, &g);
+            const double *row = resid + ((int64_t)c * n_list + i) * nr * 2;
+            double *pc = part + (size_t)c * ncell * 3;
+            for (int64_t f = 0; f < nf; ++f) {
+                double state[3] = {st[f], st[nf + f], st[2 * nf + f]};
+                double sre, sim, p, sx, sy;
+                int cell;
+                contribution_full(s, &g, n, c, f, state, r0[c], &sre, &sim, &p, &sx, &sy, &cell);
+                double gr = 0.0, gi = 0.0;
+                if (s->taps == 1) {
+                    double fk = floor(p);
+                    if (fk >= 0.0 && fk < nr) {
+                        gr = row[2 * (int)fk];
+                        gi = row[2 * (int)fk + 1];
+                    }
+                } else {
+                    int m = s->taps / 2;
+                    double fk0 = floor(p);
+                    if (fk0 >= -(double)m - 1.0 && fk0 <= (double)nr + m) {
+                        int kk0 = (int)fk0;
+                        for (int k = kk0 - m + 1; k <= kk0 + m; ++k) {
+                            if (k < 0 || k >= nr) continue;
+                            double h = or_kaiser_sinc((double)k - p, m, s->beta);
+                            gr += h * row[2 * k];
+                            gi += h * row[2 * k + 1];
+                        }
+                    }
+                }
+                double re_gs = gr * sre + gi * sim;
+                double im_gs = gr * sim - gi * sre;
+                double sig = s->cell_sigma0 ? s->cell_sigma0[cell] : s->sigma0_base;
+                if (sig > 0.0) pc[3 * cell] += re_gs / sig;
+                pc[3 * cell + 1] += 2.0 * k0 * g.t * sx * im_gs;
+                pc[3 * cell + 2] += 2.0 * k0 * g.t * sy * im_gs;
+            }
+        }
+    }
+    for (int c = 0; c < nc; ++c)
+        for (int q = 0; q < ncell; ++q) {
+            if (g_sigma) g_sigma[q] += part[((size_t)c * ncell + q) * 3];
+            if (g_uv) {
+                g_uv[2 * q] += part[((size_t)c * ncell + q) * 3 + 1];
+                g_uv[2 * q + 1] += part[((size_t)c * ncell + q) * 3 + 2];
+            }
+        }
+    free(part);
+    free(st);
+    free(kx); free(ky); free(om); free(amp); free(ph);
+    return 0;
 }
