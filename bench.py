@@ -45,6 +45,7 @@ def parse():
                     help="pulses per step (0 = the whole burst); for the slow FP64 form")
     ap.add_argument("--cpu-pulses", type=int, default=1, help="pulses in the oracle sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
     return ap.parse_args()
 
 
@@ -293,6 +294,8 @@ def main():
                 "what": "harm_scene_create + harm_echo_accumulate + IQ to pinned host memory"},
         "gpu_launches": args.steps * _launches_per_step(desc, prec, np_step),
     }
+    if prec == harm.HARM_PREC_MIXED and not args.no_adjoint:
+        line["adjoint"] = measure_adjoint(args, stream, flush)
     if not args.no_cpu:
         cpu = run_oracle_sample(desc, args.cpu_pulses)
         # IQ error of the GPU path on the sampled pulses
@@ -310,6 +313,55 @@ def main():
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def measure_adjoint(args, stream, flush):
+    """Forward and adjoint on the differentiable scene (2 km x 1 km, 1024 pulses,
+    6 channels, 100 m cells): misfit to the IQ of a Gaussian-correlated current
+    perturbation (0.1 m/s, 500 m); device time of harm_echo_accumulate and of
+    harm_echo_adjoint, same stream, L2 flushed between calls."""
+    import torch
+    from paper_2405_09938_b300 import harm
+    d = hs.adjoint_scene()
+    c = d["cells"]
+    scene = harm.harm_scene_create(d, harm.HARM_PREC_MIXED, stream)
+    s0 = torch.tensor(c["sigma0"], dtype=torch.float64, device="cuda")
+    uv = torch.tensor(c["uv"], dtype=torch.float64, device="cuda")
+    uvp = uv + torch.tensor(hs.current_perturbation(c["ncx"], c["ncy"], c["cell_m"]), device="cuda")
+    nc, npul, nr = len(d["rx"]), d["n_pulses"], d["n_range"]
+    tgt = torch.empty((nc, npul, nr), dtype=torch.complex64, device="cuda")
+    harm.harm_scene_set_cells(scene, c["ncx"], c["ncy"], c["cell_m"], s0, uvp)
+    harm.harm_echo_accumulate(scene, 0, npul, tgt)
+    harm.harm_scene_set_cells(scene, c["ncx"], c["ncy"], c["cell_m"], s0, uv)
+    iq = torch.empty_like(tgt)
+    gs, guv = torch.zeros_like(s0), torch.zeros_like(uv)
+    fwd, adj = [], []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        harm.harm_echo_accumulate(scene, 0, npul, iq)
+        b.record(stream)
+        r = iq - tgt
+        gs.zero_()
+        guv.zero_()
+        flush.zero_()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        harm.harm_echo_adjoint(scene, 0, npul, r, gs, guv)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            fwd.append(a.elapsed_time(b))
+            adj.append(c0.elapsed_time(c1))
+    harm.harm_scene_sync(scene)
+    units = hs.n_facets(d) * npul * nc
+    f_ms, a_ms = statistics.mean(fwd), statistics.mean(adj)
+    scene.close()
+    return {"workload": "adj_2x1km_1024p_6ch_100m_cells", "contributions": units, "fwd_ms": f_ms,
+            "adj_ms": a_ms, "adj_over_fwd": a_ms / f_ms, "fwd_value": units / (f_ms * 1e-3),
+            "adj_value": units / (a_ms * 1e-3), "loss": float(torch.sum(torch.abs(r) ** 2).item()),
+            "grad_uv_norm": float(torch.linalg.norm(guv).item())}
 
 
 def _launches_per_step(desc, prec, np_step):

@@ -388,13 +388,68 @@ struct FacetGeo {
     float2 z;            // speckle of the current epoch
     int epoch;           // epoch the speckle belongs to
     uint32_t fid;
+    int cell;            // cell index (per-cell fields) or -1
     bool valid;
 };
 
-template <int TAPS, typename OutT>
+// Forward sink: warp pre-reduction into the CTA range tile of the channel.
+template <typename OutT>
+struct ScatterSink {
+    float *stage;
+    float2 *tiles;  // [2][nc][WT]
+    OutT *iq;
+    int n, n0, np, buf;
+    __device__ __forceinline__ void operator()(const MixedArgs &A, int ch, const ChanRec &Q, int kb, const float h[8],
+                                               float vre, float vim, float, float, float, bool valid)
+    {
+        float2 *tile_c = tiles + (buf * A.S.nc + ch) * WT;
+        const int tile_base = Q.kbase - WT_LO;
+        OutT *grow = iq + 2 * ((size_t)ch * np + (n - n0)) * A.S.nr;
+        warp_scatter<OutT>(stage, tile_c, tile_base, kb, valid, h, vre, vim, A.S.nr, grow, A.S.flags);
+    }
+};
+
+// Adjoint sink: the transposed spread, a gather of the residual through the same
+// taps (g = sum_j h_j r[kb + j]), and the chain rule on the contribution s:
+// d/dsigma: Re(conj(g) s) / sigma;  d/d(u, v): 2 K0 t_n (r_t + r_r)_{x,y} Im(conj(g) s).
+template <typename InT>
+struct GatherSink {
+    const float2 *win;  // [nc][WT] residual window of the pulse
+    const InT *resid;
+    int n, n0, np;
+    float as, au, av;   // per-facet accumulators (sigma term, u and v terms without the factor 2)
+    __device__ __forceinline__ void operator()(const MixedArgs &A, int ch, const ChanRec &Q, int kb, const float h[8],
+                                               float vre, float vim, float qx, float qy, float k0t, bool)
+    {
+        const float2 *wc = win + ch * WT;
+        const int tb = Q.kbase - WT_LO;
+        const InT *grow = resid + 2 * ((size_t)ch * np + (n - n0)) * A.S.nr;
+        float gr = 0.0f, gi = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = kb + j;
+            const int w = k - tb;
+            float2 v;
+            if ((unsigned)w < (unsigned)WT)
+                v = wc[w];
+            else if (k >= 0 && k < A.S.nr)
+                v = make_float2((float)grow[2 * k], (float)grow[2 * k + 1]);
+            else
+                v = make_float2(0.f, 0.f);
+            gr = fmaf(h[j], v.x, gr);
+            gi = fmaf(h[j], v.y, gi);
+        }
+        const float re_gs = fmaf(gr, vre, gi * vim);
+        const float im_gs = fmaf(gr, vim, -gi * vre);
+        as += re_gs;
+        au = fmaf(-k0t * qx, im_gs, au);
+        av = fmaf(-k0t * qy, im_gs, av);
+    }
+};
+
+template <int TAPS, typename Sink>
 __device__ __forceinline__ void facet_pulse(const Smem &sm, const MixedArgs &A, const FacetGeo &G,
-                                            const float c[3][kOrders], int pi, int n, int n0, int np, int buf,
-                                            float xi_x, float fi, float *stage, OutT *iq)
+                                            const float c[3][kOrders], int pi, float xi_x, float fi, Sink &sink)
 {
     const DevScene &S = A.S;
     const int nc = S.nc;
@@ -479,10 +534,7 @@ __device__ __forceinline__ void facet_pulse(const Smem &sm, const MixedArgs &A, 
                 h[j] = v;
             }
         }
-        float2 *tile_c = sm.tile + (buf * nc + ch) * WT;
-        const int tile_base = Q.kbase - WT_LO;
-        OutT *grow = iq + 2 * ((size_t)ch * np + (n - n0)) * S.nr;
-        warp_scatter<OutT>(stage, tile_c, tile_base, kb, G.valid, h, vre, vim, S.nr, grow, S.flags);
+        sink(A, ch, Q, kb, h, vre, vim, qx, qy, PR.k0t, G.valid);
     }
 }
 
@@ -494,7 +546,8 @@ __device__ void facet_setup(const MixedArgs &A, int ix, int iy, int jref, FacetG
     G.xi_y = (float)((iy - jref) * S.dx);
     G.fid = (uint32_t)min(iy, S.ny - 1) * (uint32_t)S.nx + (uint32_t)min(ix, S.nx - 1);
     double base = S.sigma0_base, cu = S.cur_u, cv = S.cur_v;
-    if (S.cell_sigma0 || S.cell_uv) {
+    G.cell = -1;
+    if (S.ncx > 0) {
         double x = (min(ix, S.nx - 1) + 0.5 - 0.5 * S.nx) * S.dx;
         double y = (min(iy, S.ny - 1) + 0.5 - 0.5 * S.ny) * S.dx;
         int cx = (int)floor((x + 0.5 * S.nx * S.dx) / S.cell);
@@ -502,6 +555,7 @@ __device__ void facet_setup(const MixedArgs &A, int ix, int iy, int jref, FacetG
         cx = min(max(cx, 0), S.ncx - 1);
         cy = min(max(cy, 0), S.ncy - 1);
         int ci = cy * S.ncx + cx;
+        G.cell = ci;
         if (S.cell_sigma0) base = S.cell_sigma0[ci];
         if (S.cell_uv) {
             cu = S.cell_uv[2 * ci];
@@ -555,7 +609,12 @@ __global__ void __launch_bounds__(NT, 2) accumulate_mixed_kernel(MixedArgs A, in
     }
     __syncthreads();
 
-    float *stage = sm.stage + warp * SBINS * SROW;
+    ScatterSink<OutT> sink;
+    sink.stage = sm.stage + warp * SBINS * SROW;
+    sink.tiles = sm.tile;
+    sink.iq = iq;
+    sink.n0 = n0;
+    sink.np = np;
     for (int n = pa; n < pe; ++n) {
         const int pi = n - pa;
         const int buf = pi & 1;
@@ -568,8 +627,10 @@ __global__ void __launch_bounds__(NT, 2) accumulate_mixed_kernel(MixedArgs A, in
             gb.z = speckle_f(S.speckle_seed, gb.fid, (uint32_t)e);
             gb.epoch = e;
         }
-        facet_pulse<TAPS, OutT>(sm, A, ga, ca, pi, n, n0, np, buf, xi_x, fi, stage, iq);
-        facet_pulse<TAPS, OutT>(sm, A, gb, cb, pi, n, n0, np, buf, xi_x, fi, stage, iq);
+        sink.n = n;
+        sink.buf = buf;
+        facet_pulse<TAPS>(sm, A, ga, ca, pi, xi_x, fi, sink);
+        facet_pulse<TAPS>(sm, A, gb, cb, pi, xi_x, fi, sink);
         __syncthreads();
         for (int i = threadIdx.x; i < nc * WT; i += NT) {
             int ch = i / WT, w = i % WT;
@@ -581,6 +642,116 @@ __global__ void __launch_bounds__(NT, 2) accumulate_mixed_kernel(MixedArgs A, in
                 gadd<OutT>(iq + 2 * ((size_t)ch * np + (n - n0)) * S.nr, (size_t)k, v.x, v.y);
         }
     }
+}
+
+// Per-cell gradient of one facet, reduced over the warp's lanes of the same cell
+// (lanes along x: cells form contiguous lane segments) and added by the segment
+// head with FP64 atomics.
+__device__ __forceinline__ void add_cell_grads(const FacetGeo &G, float as, float au, float av, double *g_sigma,
+                                               double *g_uv)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool ok = G.valid && G.cell >= 0;
+    const int cell = ok ? G.cell : -1;
+    double vs = (ok && G.base > 0.0f) ? (double)as / (double)G.base : 0.0;
+    double vu = ok ? 2.0 * (double)au : 0.0;
+    double vv = ok ? 2.0 * (double)av : 0.0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        double ts = __shfl_down_sync(FULL, vs, d);
+        double tu = __shfl_down_sync(FULL, vu, d);
+        double tv = __shfl_down_sync(FULL, vv, d);
+        int tc = __shfl_down_sync(FULL, cell, d);
+        if (lane + d < 32 && tc == cell) {
+            vs += ts;
+            vu += tu;
+            vv += tv;
+        }
+    }
+    const int prev = __shfl_up_sync(FULL, cell, 1);
+    const bool head = (lane == 0 || prev != cell);
+    if (head && cell >= 0) {
+        if (g_sigma) atomicAdd(g_sigma + cell, vs);
+        if (g_uv) {
+            atomicAdd(g_uv + 2 * cell, vu);
+            atomicAdd(g_uv + 2 * cell + 1, vv);
+        }
+    }
+}
+
+template <int TAPS, typename InT>
+__global__ void __launch_bounds__(NT, 2)
+    adjoint_mixed_kernel(MixedArgs A, int n0, int np, int b0, const InT *resid, double *g_sigma, double *g_uv)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const DevScene &S = A.S;
+    const int nc = S.nc;
+    const Smem sm = carve(smem_raw, nc);
+    const int tiles_x = (S.nx + TX - 1) / TX;
+    const int tx0 = (blockIdx.x % tiles_x) * TX;
+    const int ty0 = (blockIdx.x / tiles_x) * TY;
+    const int batch = b0 + blockIdx.y;
+    const int pa = max(n0, batch * A.nb);
+    const int pe = min(n0 + np, (batch + 1) * A.nb);
+    if (pa >= pe) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ix = tx0 + lane;
+    const int iref = tx0 + TX / 2, jref = ty0 + TY / 2;
+    const double xr = (iref + 0.5 - 0.5 * S.nx) * S.dx;
+    const double yr = (jref + 0.5 - 0.5 * S.ny) * S.dx;
+    const float xi_x = (float)((ix - iref) * S.dx);
+    const float fi = (float)(ix - iref);
+
+    build_refs(sm, A, pa, pe, xr, yr);
+    FacetGeo ga, gb;
+    facet_setup(A, ix, ty0 + warp, jref, ga);
+    facet_setup(A, ix, ty0 + warp + NWARP, jref, gb);
+    float ca[3][kOrders], cb[3][kOrders];
+    if (!S.static_surface && S.nw > 0) {
+        taylor_coeffs(sm, A, batch, ix, ty0 + warp, ty0 + warp + NWARP, ca, cb);
+    } else {
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int o = 0; o < kOrders; ++o) ca[f][o] = cb[f][o] = 0.0f;
+    }
+    GatherSink<InT> ka, kb;
+    ka.win = kb.win = sm.tile;
+    ka.resid = kb.resid = resid;
+    ka.n0 = kb.n0 = n0;
+    ka.np = kb.np = np;
+    ka.as = ka.au = ka.av = kb.as = kb.au = kb.av = 0.0f;
+    for (int n = pa; n < pe; ++n) {
+        const int pi = n - pa;
+        __syncthreads();
+        // residual window of this pulse, every channel
+        for (int i = threadIdx.x; i < nc * WT; i += NT) {
+            int ch = i / WT, w = i % WT;
+            int k = sm.ch[pi * nc + ch].kbase - WT_LO + w;
+            float2 v = make_float2(0.f, 0.f);
+            if (k >= 0 && k < S.nr) {
+                const InT *r = resid + 2 * (((size_t)ch * np + (n - n0)) * S.nr + k);
+                v = make_float2((float)r[0], (float)r[1]);
+            }
+            sm.tile[i] = v;
+        }
+        __syncthreads();
+        const int e = sm.pr[pi].epoch;
+        if (e != ga.epoch) {
+            ga.z = speckle_f(S.speckle_seed, ga.fid, (uint32_t)e);
+            ga.epoch = e;
+        }
+        if (e != gb.epoch) {
+            gb.z = speckle_f(S.speckle_seed, gb.fid, (uint32_t)e);
+            gb.epoch = e;
+        }
+        ka.n = kb.n = n;
+        facet_pulse<TAPS>(sm, A, ga, ca, pi, xi_x, fi, ka);
+        facet_pulse<TAPS>(sm, A, gb, cb, pi, xi_x, fi, kb);
+    }
+    add_cell_grads(ga, ka.as, ka.au, ka.av, g_sigma, g_uv);
+    add_cell_grads(gb, kb.as, kb.au, kb.av, g_sigma, g_uv);
 }
 
 // Facet generator of the mixed path: same Taylor expansion, states written out.
@@ -709,6 +880,43 @@ cudaError_t launch_accumulate_mixed(const DevScene &S, const MixedTables &M, cud
             } else {
                 if ((e = prep(accumulate_mixed_kernel<8, double>, bytes)) != cudaSuccess) return e;
                 accumulate_mixed_kernel<8, double><<<grid, NT, bytes, st>>>(A, n0, np, bb, (double *)iq);
+            }
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_adjoint_mixed(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np,
+                                 const void *resid, harm_dtype dtype, double *g_sigma, double *g_uv)
+{
+    MixedArgs A = make_args(S, M);
+    const int bytes = layout(S.nc).total;
+    int tiles = ((S.nx + TX - 1) / TX) * ((S.ny + TY - 1) / TY);
+    int b0 = n0 / M.nb, b1 = (n0 + np - 1) / M.nb;
+    cudaError_t e;
+    for (int bb = b0; bb <= b1; bb += 65535) {
+        int cnt = min(65535, b1 - bb + 1);
+        dim3 grid(tiles, cnt);
+        if (dtype == HARM_C64) {
+            if (S.taps == 1) {
+                if ((e = prep(adjoint_mixed_kernel<1, float>, bytes)) != cudaSuccess) return e;
+                adjoint_mixed_kernel<1, float><<<grid, NT, bytes, st>>>(A, n0, np, bb, (const float *)resid,
+                                                                         g_sigma, g_uv);
+            } else {
+                if ((e = prep(adjoint_mixed_kernel<8, float>, bytes)) != cudaSuccess) return e;
+                adjoint_mixed_kernel<8, float><<<grid, NT, bytes, st>>>(A, n0, np, bb, (const float *)resid,
+                                                                         g_sigma, g_uv);
+            }
+        } else {
+            if (S.taps == 1) {
+                if ((e = prep(adjoint_mixed_kernel<1, double>, bytes)) != cudaSuccess) return e;
+                adjoint_mixed_kernel<1, double><<<grid, NT, bytes, st>>>(A, n0, np, bb, (const double *)resid,
+                                                                          g_sigma, g_uv);
+            } else {
+                if ((e = prep(adjoint_mixed_kernel<8, double>, bytes)) != cudaSuccess) return e;
+                adjoint_mixed_kernel<8, double><<<grid, NT, bytes, st>>>(A, n0, np, bb, (const double *)resid,
+                                                                          g_sigma, g_uv);
             }
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

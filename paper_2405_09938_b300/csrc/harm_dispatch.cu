@@ -176,9 +176,11 @@ cudaError_t launch_accumulate(harm_scene *s, int n0, int np, void *iq, harm_dtyp
     return launch_accumulate_mixed(s->dev, s->mixed, s->stream, n0, np, iq, dtype);
 }
 
-cudaError_t launch_adjoint(harm_scene *, int, int, const void *, harm_dtype, double *, double *)
+cudaError_t launch_adjoint(harm_scene *s, int n0, int np, const void *resid, harm_dtype dtype, double *g_sigma,
+                           double *g_uv)
 {
-    return cudaErrorNotSupported;
+    if (s->desc.precision != HARM_PREC_MIXED) return cudaErrorNotSupported;
+    return launch_adjoint_mixed(s->dev, s->mixed, s->stream, n0, np, resid, dtype, g_sigma, g_uv);
 }
 
 }  // namespace harm

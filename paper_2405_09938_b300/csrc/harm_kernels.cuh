@@ -64,5 +64,7 @@ cudaError_t launch_generate_mixed(const DevScene &S, const MixedTables &M, cudaS
                                   float *state);
 cudaError_t launch_accumulate_mixed(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np,
                                     void *iq, harm_dtype dtype);
+cudaError_t launch_adjoint_mixed(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np,
+                                 const void *resid, harm_dtype dtype, double *g_sigma, double *g_uv);
 
 }  // namespace harm
