@@ -162,6 +162,40 @@ harm_status harm_echo_accumulate(harm_scene *scene, int32_t n0, int32_t np, void
 harm_status harm_echo_adjoint(harm_scene *scene, int32_t n0, int32_t np, const void *resid_dev,
                               harm_dtype dtype, double *grad_sigma0_dev, double *grad_uv_dev);
 
+/* ----------------------------------------------------------------------------
+   Batched scenes (Sec. IV-B: the scene is processed as a batch of tiles; here a
+   batch of independent scenes of uneven size runs as one persistent launch).
+   ------------------------------------------------------------------------- */
+typedef struct harm_batch harm_batch; /* opaque, owned by the library */
+
+/* Group n_scenes mixed-precision scenes (same device, same channel count, same
+   taps and Kaiser beta) into one batched forward launch on the first scene's
+   stream. The batch keeps pointers to the scenes: they must outlive it. The work
+   list is every (scene, 32 x rows facet tile, 32-pulse batch) item over the full
+   burst of every scene, largest scenes first. Errors: HARM_E_INVALID (NULL,
+   n_scenes < 1, mixed devices, channel counts or tap settings),
+   HARM_E_UNSUPPORTED (an FP64 scene), HARM_E_OOM, HARM_E_CUDA. */
+harm_status harm_batch_create(harm_scene *const *scenes, int32_t n_scenes, harm_batch **out);
+
+/* Autotuner: times the persistent launch with tile heights of 8 and 16 facet rows
+   on the first pulse batches of each scene-size class and keeps the faster per
+   class. iq_dev[s] are the scenes' complex64 IQ buffers [n_channels][n_pulses]
+   [n_range] (device); their contents are overwritten. Synchronous. */
+harm_status harm_batch_tune(harm_batch *batch, void *const *iq_dev);
+
+/* Tile heights chosen for each scene (rows[n_scenes], host memory). */
+harm_status harm_batch_tile_rows(const harm_batch *batch, int32_t *rows);
+
+/* Echo of every scene over its full burst into iq_dev[s] (complex64, device),
+   as one persistent launch replayed from a CUDA graph; the graph is captured on
+   the first call and again whenever the output pointers or zero_first change.
+   zero_first = 1 clears the outputs first (inside the graph). Asynchronous on
+   the batch's stream. */
+harm_status harm_batch_run(harm_batch *batch, void *const *iq_dev, int32_t zero_first);
+
+/* Release the batch (waits for its stream). NULL is OK. */
+harm_status harm_batch_destroy(harm_batch *batch);
+
 /* Wait for the scene's stream and report device-side errors (bounded waits that
    timed out, bounds flags) raised since the last check. */
 harm_status harm_scene_sync(harm_scene *scene);

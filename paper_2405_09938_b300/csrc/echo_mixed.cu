@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <climits>
+#include <cstring>
 
 #include "harm_internal.cuh"
 #include "harm_kernels.cuh"
@@ -77,6 +78,12 @@ struct MixedArgs {
     float tx_laz_l, tx_lel_l;  // aperture / wavelength
     float rx_laz_l[kMaxCh], rx_lel_l[kMaxCh];
     float wcos, wsin, wind_mod, area, k0, inv_dr;
+};
+
+// Polynomial tables shared by every scene of a launch (they depend only on the
+// Kaiser beta): passed as kernel parameters so the inner loops read them from
+// the constant bank.
+struct PolyArgs {
     float tap[8][kTapDeg + 1];
     float sinc2[kSincDeg + 1];
 };
@@ -130,14 +137,14 @@ __device__ __forceinline__ Smem carve(unsigned char *raw, int nc)
 
 // sinc^2(x): polynomial for |x| <= 1 (main lobe and the start of the first
 // sidelobe), sin(pi x) / (pi x) otherwise.
-__device__ __forceinline__ float sinc2f(const MixedArgs &A, float x)
+__device__ __forceinline__ float sinc2f(const PolyArgs &P, float x)
 {
     float u = x * x;
     if (u <= 1.0f) {
         float t = fmaf(2.0f, u, -1.0f);
-        float r = A.sinc2[kSincDeg];
+        float r = P.sinc2[kSincDeg];
 #pragma unroll
-        for (int d = kSincDeg - 1; d >= 0; --d) r = fmaf(r, t, A.sinc2[d]);
+        for (int d = kSincDeg - 1; d >= 0; --d) r = fmaf(r, t, P.sinc2[d]);
         return r;
     }
     float s = __fdividef(sinpif(x), kPiF * x);
@@ -235,7 +242,7 @@ __device__ void build_refs(const Smem &sm, const MixedArgs &A, int pa, int pe, d
 
 // Taylor coefficients of (eta, eta_x, eta_y) in time for two facets (column ix,
 // rows iya / iyb), accumulated over the wave components in shared-memory chunks.
-__device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int ix, int iya, int iyb,
+__device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int ix, int iya, int iyb, bool two,
                               float ca[3][kOrders], float cb[3][kOrders])
 {
     const DevScene &S = A.S;
@@ -258,14 +265,24 @@ __device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int
             float qar = e.x * ya.x - e.y * ya.y, qai = e.x * ya.y + e.y * ya.x;
             float qbr = e.x * yb.x - e.y * yb.y, qbi = e.x * yb.y + e.y * yb.x;
             const float2 *wm = sm.w + m * 3 * kOrders;
+            if (two) {
 #pragma unroll
-            for (int f = 0; f < 3; ++f)
+                for (int f = 0; f < 3; ++f)
 #pragma unroll
-                for (int o = 0; o < kOrders; ++o) {
-                    float2 w = wm[f * kOrders + o];
-                    ca[f][o] = fmaf(qar, w.x, fmaf(-qai, w.y, ca[f][o]));
-                    cb[f][o] = fmaf(qbr, w.x, fmaf(-qbi, w.y, cb[f][o]));
-                }
+                    for (int o = 0; o < kOrders; ++o) {
+                        float2 w = wm[f * kOrders + o];
+                        ca[f][o] = fmaf(qar, w.x, fmaf(-qai, w.y, ca[f][o]));
+                        cb[f][o] = fmaf(qbr, w.x, fmaf(-qbi, w.y, cb[f][o]));
+                    }
+            } else {
+#pragma unroll
+                for (int f = 0; f < 3; ++f)
+#pragma unroll
+                    for (int o = 0; o < kOrders; ++o) {
+                        float2 w = wm[f * kOrders + o];
+                        ca[f][o] = fmaf(qar, w.x, fmaf(-qai, w.y, ca[f][o]));
+                    }
+            }
         }
     }
 }
@@ -448,8 +465,9 @@ struct GatherSink {
 };
 
 template <int TAPS, typename Sink>
-__device__ __forceinline__ void facet_pulse(const Smem &sm, const MixedArgs &A, const FacetGeo &G,
-                                            const float c[3][kOrders], int pi, float xi_x, float fi, Sink &sink)
+__device__ __forceinline__ void facet_pulse(const Smem &sm, const MixedArgs &A, const PolyArgs &P,
+                                            const FacetGeo &G, const float c[3][kOrders], int pi, float xi_x,
+                                            float fi, Sink &sink)
 {
     const DevScene &S = A.S;
     const int nc = S.nc;
@@ -471,7 +489,7 @@ __device__ __forceinline__ void facet_pulse(const Smem &sm, const MixedArgs &A, 
     const float rho_t = fmaf(et, et, 1.0f - et);
     const float ut = (T.u0 + fmaf(xi0, T.aRx, fmaf(xi1, T.aRy, xi2 * T.aRz))) * rho_t;
     const float vt = (T.v0 + fmaf(xi0, T.eRx, fmaf(xi1, T.eRy, xi2 * T.eRz))) * rho_t;
-    const float gt = sinc2f(A, A.tx_laz_l * ut) * sinc2f(A, A.tx_lel_l * vt);
+    const float gt = sinc2f(P, A.tx_laz_l * ut) * sinc2f(P, A.tx_lel_l * vt);
     const float rt0 = fmaf(xi0, T.invR, T.ux) * rho_t;
     const float rt1 = fmaf(xi1, T.invR, T.uy) * rho_t;
     const float rt2 = fmaf(xi2, T.invR, T.uz) * rho_t;
@@ -490,7 +508,7 @@ __device__ __forceinline__ void facet_pulse(const Smem &sm, const MixedArgs &A, 
         const float rho_r = fmaf(er, er, 1.0f - er);
         const float ur = (R.u0 + fmaf(xi0, R.aRx, fmaf(xi1, R.aRy, xi2 * R.aRz))) * rho_r;
         const float vr = (R.v0 + fmaf(xi0, R.eRx, fmaf(xi1, R.eRy, xi2 * R.eRz))) * rho_r;
-        const float gr = sinc2f(A, A.rx_laz_l[ch] * ur) * sinc2f(A, A.rx_lel_l[ch] * vr);
+        const float gr = sinc2f(P, A.rx_laz_l[ch] * ur) * sinc2f(P, A.rx_lel_l[ch] * vr);
         const float qx = -fmaf(fmaf(xi0, R.invR, R.ux), rho_r, rt0);
         const float qy = -fmaf(fmaf(xi1, R.invR, R.uy), rho_r, rt1);
         const float qz = -fmaf(fmaf(xi2, R.invR, R.uz), rho_r, rt2);
@@ -528,9 +546,9 @@ __device__ __forceinline__ void facet_pulse(const Smem &sm, const MixedArgs &A, 
             const float t = fmaf(2.0f, fr, -1.0f);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                float v = A.tap[j][kTapDeg];
+                float v = P.tap[j][kTapDeg];
 #pragma unroll
-                for (int d = kTapDeg - 1; d >= 0; --d) v = fmaf(v, t, A.tap[j][d]);
+                for (int d = kTapDeg - 1; d >= 0; --d) v = fmaf(v, t, P.tap[j][d]);
                 h[j] = v;
             }
         }
@@ -569,38 +587,49 @@ __device__ void facet_setup(const MixedArgs &A, int ix, int iy, int jref, FacetG
     G.z = make_float2(0.f, 0.f);
 }
 
-template <int TAPS, typename OutT>
-__global__ void __launch_bounds__(NT, 2) accumulate_mixed_kernel(MixedArgs A, int n0, int np, int b0, OutT *iq)
+// Tile geometry of one work item: 32 columns x ty rows (ty = 8 or 16) of the
+// scene's facet grid; warp w handles rows w and (ty = 16) w + 8.
+struct ItemGeo {
+    int tx0, ty0, ty, pa, pe, batch;
+};
+
+__device__ __forceinline__ ItemGeo item_geo(const MixedArgs &A, int tile, int batch, int ty, int n0, int np)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ItemGeo g;
+    const int tiles_x = (A.S.nx + TX - 1) / TX;
+    g.tx0 = (tile % tiles_x) * TX;
+    g.ty0 = (tile / tiles_x) * ty;
+    g.ty = ty;
+    g.batch = batch;
+    g.pa = max(n0, batch * A.nb);
+    g.pe = min(n0 + np, (batch + 1) * A.nb);
+    return g;
+}
+
+// One forward work item (tile x pulse batch) of one scene. Every thread of the
+// CTA calls it; it starts and ends with the CTA's range tiles all zero.
+template <int TAPS, typename OutT>
+__device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs &P, const ItemGeo &I, int n0, int np,
+                             OutT *iq)
+{
     const DevScene &S = A.S;
     const int nc = S.nc;
-    const Smem sm = carve(smem_raw, nc);
-    const int tiles_x = (S.nx + TX - 1) / TX;
-    const int tx0 = (blockIdx.x % tiles_x) * TX;
-    const int ty0 = (blockIdx.x / tiles_x) * TY;
-    const int batch = b0 + blockIdx.y;
-    const int pa = max(n0, batch * A.nb);
-    const int pe = min(n0 + np, (batch + 1) * A.nb);
-    if (pa >= pe) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ix = tx0 + lane;
-    const int iref = tx0 + TX / 2, jref = ty0 + TY / 2;
+    const bool two = I.ty > NWARP;
+    const int ix = I.tx0 + lane;
+    const int iref = I.tx0 + TX / 2, jref = I.ty0 + I.ty / 2;
     const double xr = (iref + 0.5 - 0.5 * S.nx) * S.dx;
     const double yr = (jref + 0.5 - 0.5 * S.ny) * S.dx;
     const float xi_x = (float)((ix - iref) * S.dx);
     const float fi = (float)(ix - iref);
 
-    for (int i = threadIdx.x; i < 2 * nc * WT; i += NT) sm.tile[i] = make_float2(0.f, 0.f);
-    for (int i = threadIdx.x; i < NWARP * SBINS * SROW; i += NT) sm.stage[i] = 0.0f;
-    build_refs(sm, A, pa, pe, xr, yr);
-
+    build_refs(sm, A, I.pa, I.pe, xr, yr);
     FacetGeo ga, gb;
-    facet_setup(A, ix, ty0 + warp, jref, ga);
-    facet_setup(A, ix, ty0 + warp + NWARP, jref, gb);
+    facet_setup(A, ix, I.ty0 + warp, jref, ga);
+    facet_setup(A, ix, I.ty0 + warp + NWARP, jref, gb);
     float ca[3][kOrders], cb[3][kOrders];
     if (!S.static_surface && S.nw > 0) {
-        taylor_coeffs(sm, A, batch, ix, ty0 + warp, ty0 + warp + NWARP, ca, cb);
+        taylor_coeffs(sm, A, I.batch, ix, I.ty0 + warp, I.ty0 + warp + NWARP, two, ca, cb);
     } else {
 #pragma unroll
         for (int f = 0; f < 3; ++f)
@@ -615,22 +644,24 @@ __global__ void __launch_bounds__(NT, 2) accumulate_mixed_kernel(MixedArgs A, in
     sink.iq = iq;
     sink.n0 = n0;
     sink.np = np;
-    for (int n = pa; n < pe; ++n) {
-        const int pi = n - pa;
+    for (int n = I.pa; n < I.pe; ++n) {
+        const int pi = n - I.pa;
         const int buf = pi & 1;
         const int e = sm.pr[pi].epoch;
         if (e != ga.epoch) {
             ga.z = speckle_f(S.speckle_seed, ga.fid, (uint32_t)e);
             ga.epoch = e;
         }
-        if (e != gb.epoch) {
-            gb.z = speckle_f(S.speckle_seed, gb.fid, (uint32_t)e);
-            gb.epoch = e;
-        }
         sink.n = n;
         sink.buf = buf;
-        facet_pulse<TAPS>(sm, A, ga, ca, pi, xi_x, fi, sink);
-        facet_pulse<TAPS>(sm, A, gb, cb, pi, xi_x, fi, sink);
+        facet_pulse<TAPS>(sm, A, P, ga, ca, pi, xi_x, fi, sink);
+        if (two) {
+            if (e != gb.epoch) {
+                gb.z = speckle_f(S.speckle_seed, gb.fid, (uint32_t)e);
+                gb.epoch = e;
+            }
+            facet_pulse<TAPS>(sm, A, P, gb, cb, pi, xi_x, fi, sink);
+        }
         __syncthreads();
         for (int i = threadIdx.x; i < nc * WT; i += NT) {
             int ch = i / WT, w = i % WT;
@@ -641,6 +672,92 @@ __global__ void __launch_bounds__(NT, 2) accumulate_mixed_kernel(MixedArgs A, in
             if ((v.x != 0.0f || v.y != 0.0f) && k >= 0 && k < S.nr)
                 gadd<OutT>(iq + 2 * ((size_t)ch * np + (n - n0)) * S.nr, (size_t)k, v.x, v.y);
         }
+    }
+    // the other buffer was flushed one pulse earlier; make sure every thread is
+    // done with the tiles and the records before they are reused
+    __syncthreads();
+}
+
+__device__ __forceinline__ void clear_smem(const Smem &sm, int nc)
+{
+    for (int i = threadIdx.x; i < 2 * nc * WT; i += NT) sm.tile[i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < NWARP * SBINS * SROW; i += NT) sm.stage[i] = 0.0f;
+}
+
+template <int TAPS, typename OutT>
+__global__ void __launch_bounds__(NT, 2)
+    accumulate_mixed_kernel(MixedArgs A, PolyArgs P, int n0, int np, int b0, int ty, OutT *iq)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Smem sm = carve(smem_raw, A.S.nc);
+    const ItemGeo I = item_geo(A, blockIdx.x, b0 + blockIdx.y, ty, n0, np);
+    if (I.pa >= I.pe) return;
+    clear_smem(sm, A.S.nc);
+    forward_item<TAPS, OutT>(sm, A, P, I, n0, np, iq);
+}
+
+// Work list of a batched launch: scene s owns items [start[s], start[s + 1]);
+// item i of scene s is (batch = i / tiles[s], tile = i % tiles[s]) so that
+// consecutive items share the pulse batch (IQ rows stay in L2).
+struct BatchItems {
+    const MixedArgs *args;  // [n] per-scene arguments (device)
+    const int *start;       // [n + 1] prefix sums of items
+    const int *tiles;       // [n] tiles per batch
+    const int *ty;          // [n] tile height (8 or 16), chosen by the autotuner
+    const int *order;       // [n] processing order of the scenes (largest first)
+    float *const *iq;       // [n] IQ outputs (complex64)
+    int n;
+    int total;
+};
+
+// Persistent batched forward launch: a fixed pool of CTAs pulls work items from
+// a global counter until the list is exhausted (no waiting on other CTAs). The
+// scene arguments of the current item are copied to shared memory.
+template <int TAPS>
+__global__ void __launch_bounds__(NT, 2) batch_mixed_kernel(BatchItems B, PolyArgs P, unsigned int *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ MixedArgs args;
+    __shared__ int s_item, s_scene;
+    const int nc_max = B.args[0].S.nc;  // layout sized for the first scene's channels (all equal)
+    const Smem sm = carve(smem_raw, nc_max);
+    int cur_scene = -1;
+    clear_smem(sm, nc_max);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int it = (int)atomicAdd(counter, 1u);
+            s_item = it;
+            int sc = -1;
+            if (it < B.total) {
+                // scenes are laid out in processing order: find k with start[k] <= it < start[k+1]
+                int lo = 0, hi = B.n - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (B.start[mid] <= it)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+                sc = lo;
+            }
+            s_scene = sc;
+        }
+        __syncthreads();
+        const int it = s_item, k = s_scene;
+        if (it >= B.total) break;
+        const int scene = B.order[k];
+        if (scene != cur_scene) {
+            const int *src = reinterpret_cast<const int *>(B.args + scene);
+            int *dst = reinterpret_cast<int *>(&args);
+            for (int i = threadIdx.x; i < (int)(sizeof(MixedArgs) / 4); i += NT) dst[i] = src[i];
+            cur_scene = scene;
+        }
+        __syncthreads();
+        const int local = it - B.start[k];
+        const int tiles = B.tiles[scene];
+        const ItemGeo I = item_geo(args, local % tiles, local / tiles, B.ty[scene], 0, args.S.np_total);
+        if (I.pa < I.pe) forward_item<TAPS, float>(sm, args, P, I, 0, args.S.np_total, B.iq[scene]);
+        __syncthreads();
     }
 }
 
@@ -682,7 +799,8 @@ __device__ __forceinline__ void add_cell_grads(const FacetGeo &G, float as, floa
 
 template <int TAPS, typename InT>
 __global__ void __launch_bounds__(NT, 2)
-    adjoint_mixed_kernel(MixedArgs A, int n0, int np, int b0, const InT *resid, double *g_sigma, double *g_uv)
+    adjoint_mixed_kernel(MixedArgs A, PolyArgs P, int n0, int np, int b0, const InT *resid, double *g_sigma,
+                         double *g_uv)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DevScene &S = A.S;
@@ -709,7 +827,7 @@ __global__ void __launch_bounds__(NT, 2)
     facet_setup(A, ix, ty0 + warp + NWARP, jref, gb);
     float ca[3][kOrders], cb[3][kOrders];
     if (!S.static_surface && S.nw > 0) {
-        taylor_coeffs(sm, A, batch, ix, ty0 + warp, ty0 + warp + NWARP, ca, cb);
+        taylor_coeffs(sm, A, batch, ix, ty0 + warp, ty0 + warp + NWARP, true, ca, cb);
     } else {
 #pragma unroll
         for (int f = 0; f < 3; ++f)
@@ -747,8 +865,8 @@ __global__ void __launch_bounds__(NT, 2)
             gb.epoch = e;
         }
         ka.n = kb.n = n;
-        facet_pulse<TAPS>(sm, A, ga, ca, pi, xi_x, fi, ka);
-        facet_pulse<TAPS>(sm, A, gb, cb, pi, xi_x, fi, kb);
+        facet_pulse<TAPS>(sm, A, P, ga, ca, pi, xi_x, fi, ka);
+        facet_pulse<TAPS>(sm, A, P, gb, cb, pi, xi_x, fi, kb);
     }
     add_cell_grads(ga, ka.as, ka.au, ka.av, g_sigma, g_uv);
     add_cell_grads(gb, kb.as, kb.au, kb.av, g_sigma, g_uv);
@@ -773,7 +891,7 @@ __global__ void __launch_bounds__(NT, 2) generate_mixed_kernel(MixedArgs A, int 
     const bool va = ix < S.nx && iya < S.ny, vb = ix < S.nx && iyb < S.ny;
     float ca[3][kOrders], cb[3][kOrders];
     if (!S.static_surface && S.nw > 0) {
-        taylor_coeffs(sm, A, batch, ix, iya, iyb, ca, cb);
+        taylor_coeffs(sm, A, batch, ix, iya, iyb, true, ca, cb);
     } else {
 #pragma unroll
         for (int f = 0; f < 3; ++f)
@@ -821,10 +939,16 @@ MixedArgs make_args(const DevScene &S, const MixedTables &M)
     A.area = (float)S.area;
     A.k0 = (float)S.k0;
     A.inv_dr = (float)S.inv_dr;
-    for (int j = 0; j < 8; ++j)
-        for (int d = 0; d <= kTapDeg; ++d) A.tap[j][d] = M.tap[j][d];
-    for (int d = 0; d <= kSincDeg; ++d) A.sinc2[d] = M.sinc2[d];
     return A;
+}
+
+PolyArgs make_poly(const MixedTables &M)
+{
+    PolyArgs P;
+    for (int j = 0; j < 8; ++j)
+        for (int d = 0; d <= kTapDeg; ++d) P.tap[j][d] = M.tap[j][d];
+    for (int d = 0; d <= kSincDeg; ++d) P.sinc2[d] = M.sinc2[d];
+    return P;
 }
 
 template <typename K>
@@ -858,8 +982,10 @@ cudaError_t launch_accumulate_mixed(const DevScene &S, const MixedTables &M, cud
                                     void *iq, harm_dtype dtype)
 {
     MixedArgs A = make_args(S, M);
+    PolyArgs P = make_poly(M);
     const int bytes = layout(S.nc).total;
-    int tiles = ((S.nx + TX - 1) / TX) * ((S.ny + TY - 1) / TY);
+    const int ty = TY;
+    int tiles = ((S.nx + TX - 1) / TX) * ((S.ny + ty - 1) / ty);
     int b0 = n0 / M.nb, b1 = (n0 + np - 1) / M.nb;
     cudaError_t e;
     for (int bb = b0; bb <= b1; bb += 65535) {
@@ -868,18 +994,18 @@ cudaError_t launch_accumulate_mixed(const DevScene &S, const MixedTables &M, cud
         if (dtype == HARM_C64) {
             if (S.taps == 1) {
                 if ((e = prep(accumulate_mixed_kernel<1, float>, bytes)) != cudaSuccess) return e;
-                accumulate_mixed_kernel<1, float><<<grid, NT, bytes, st>>>(A, n0, np, bb, (float *)iq);
+                accumulate_mixed_kernel<1, float><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, ty, (float *)iq);
             } else {
                 if ((e = prep(accumulate_mixed_kernel<8, float>, bytes)) != cudaSuccess) return e;
-                accumulate_mixed_kernel<8, float><<<grid, NT, bytes, st>>>(A, n0, np, bb, (float *)iq);
+                accumulate_mixed_kernel<8, float><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, ty, (float *)iq);
             }
         } else {
             if (S.taps == 1) {
                 if ((e = prep(accumulate_mixed_kernel<1, double>, bytes)) != cudaSuccess) return e;
-                accumulate_mixed_kernel<1, double><<<grid, NT, bytes, st>>>(A, n0, np, bb, (double *)iq);
+                accumulate_mixed_kernel<1, double><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, ty, (double *)iq);
             } else {
                 if ((e = prep(accumulate_mixed_kernel<8, double>, bytes)) != cudaSuccess) return e;
-                accumulate_mixed_kernel<8, double><<<grid, NT, bytes, st>>>(A, n0, np, bb, (double *)iq);
+                accumulate_mixed_kernel<8, double><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, ty, (double *)iq);
             }
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -891,6 +1017,7 @@ cudaError_t launch_adjoint_mixed(const DevScene &S, const MixedTables &M, cudaSt
                                  const void *resid, harm_dtype dtype, double *g_sigma, double *g_uv)
 {
     MixedArgs A = make_args(S, M);
+    PolyArgs P = make_poly(M);
     const int bytes = layout(S.nc).total;
     int tiles = ((S.nx + TX - 1) / TX) * ((S.ny + TY - 1) / TY);
     int b0 = n0 / M.nb, b1 = (n0 + np - 1) / M.nb;
@@ -901,21 +1028,21 @@ cudaError_t launch_adjoint_mixed(const DevScene &S, const MixedTables &M, cudaSt
         if (dtype == HARM_C64) {
             if (S.taps == 1) {
                 if ((e = prep(adjoint_mixed_kernel<1, float>, bytes)) != cudaSuccess) return e;
-                adjoint_mixed_kernel<1, float><<<grid, NT, bytes, st>>>(A, n0, np, bb, (const float *)resid,
+                adjoint_mixed_kernel<1, float><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, (const float *)resid,
                                                                          g_sigma, g_uv);
             } else {
                 if ((e = prep(adjoint_mixed_kernel<8, float>, bytes)) != cudaSuccess) return e;
-                adjoint_mixed_kernel<8, float><<<grid, NT, bytes, st>>>(A, n0, np, bb, (const float *)resid,
+                adjoint_mixed_kernel<8, float><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, (const float *)resid,
                                                                          g_sigma, g_uv);
             }
         } else {
             if (S.taps == 1) {
                 if ((e = prep(adjoint_mixed_kernel<1, double>, bytes)) != cudaSuccess) return e;
-                adjoint_mixed_kernel<1, double><<<grid, NT, bytes, st>>>(A, n0, np, bb, (const double *)resid,
+                adjoint_mixed_kernel<1, double><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, (const double *)resid,
                                                                           g_sigma, g_uv);
             } else {
                 if ((e = prep(adjoint_mixed_kernel<8, double>, bytes)) != cudaSuccess) return e;
-                adjoint_mixed_kernel<8, double><<<grid, NT, bytes, st>>>(A, n0, np, bb, (const double *)resid,
+                adjoint_mixed_kernel<8, double><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, (const double *)resid,
                                                                           g_sigma, g_uv);
             }
         }
@@ -925,5 +1052,52 @@ cudaError_t launch_adjoint_mixed(const DevScene &S, const MixedTables &M, cudaSt
 }
 
 int mixed_batch_pulses() { return NBMAX; }
+
+// ---------------------------------------------------------------------------
+// Batched persistent launch (host side)
+// ---------------------------------------------------------------------------
+size_t batch_args_bytes() { return sizeof(MixedArgs); }
+
+void batch_fill_args(const harm_scene *s, void *dst)
+{
+    MixedArgs A = make_args(s->dev, s->mixed);
+    memcpy(dst, &A, sizeof(MixedArgs));
+}
+
+int batch_tiles(const harm_scene *s, int ty)
+{
+    return ((s->desc.nx + TX - 1) / TX) * ((s->desc.ny + ty - 1) / ty);
+}
+
+int batch_ctas(int device)
+{
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    return 2 * sms;
+}
+
+cudaError_t batch_launch(const BatchLaunch &L, cudaStream_t st)
+{
+    BatchItems B;
+    B.args = reinterpret_cast<const MixedArgs *>(L.args);
+    B.start = L.start;
+    B.tiles = L.tiles;
+    B.ty = L.ty;
+    B.order = L.order;
+    B.iq = L.iq;
+    B.n = L.n;
+    B.total = L.total;
+    PolyArgs P = make_poly(*L.poly);
+    const int bytes = layout(L.nc).total;
+    cudaError_t e;
+    if (L.taps == 1) {
+        if ((e = prep(batch_mixed_kernel<1>, bytes)) != cudaSuccess) return e;
+        batch_mixed_kernel<1><<<L.ctas, NT, bytes, st>>>(B, P, L.counter);
+    } else {
+        if ((e = prep(batch_mixed_kernel<8>, bytes)) != cudaSuccess) return e;
+        batch_mixed_kernel<8><<<L.ctas, NT, bytes, st>>>(B, P, L.counter);
+    }
+    return cudaGetLastError();
+}
 
 }  // namespace harm

@@ -64,6 +64,24 @@ cudaError_t launch_generate_mixed(const DevScene &S, const MixedTables &M, cudaS
                                   float *state);
 cudaError_t launch_accumulate_mixed(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np,
                                     void *iq, harm_dtype dtype);
+// Device-side description of a batched launch (arrays in device memory).
+struct BatchLaunch {
+    const void *args;        // [n] per-scene kernel arguments (opaque, batch_args_bytes() each)
+    const int *start;        // [n + 1] item prefix sums in processing order
+    const int *tiles;        // [n] tiles per pulse batch (by scene)
+    const int *ty;           // [n] tile rows (8 or 16, by scene)
+    const int *order;        // [n] scene processed at position k
+    float *const *iq;        // [n] complex64 outputs (by scene)
+    unsigned int *counter;   // work counter (zeroed before the launch)
+    const MixedTables *poly; // tap / sinc polynomials (shared)
+    int n, total, nc, taps, ctas;
+};
+size_t batch_args_bytes();
+void batch_fill_args(const harm_scene *s, void *dst);
+int batch_tiles(const harm_scene *s, int ty);
+int batch_ctas(int device);
+cudaError_t batch_launch(const BatchLaunch &L, cudaStream_t st);
+
 cudaError_t launch_adjoint_mixed(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np,
                                  const void *resid, harm_dtype dtype, double *g_sigma, double *g_uv);
 

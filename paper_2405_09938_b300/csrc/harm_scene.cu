@@ -274,6 +274,14 @@ harm_status check_ptr(const void *p, const char *what)
 
 }  // namespace
 
+namespace harm {
+harm_status set_error(harm_status s, const char *msg)
+{
+    g_last_error = msg;
+    return s;
+}
+}  // namespace harm
+
 extern "C" {
 
 const char *harm_last_error(void) { return g_last_error.c_str(); }

@@ -78,6 +78,11 @@ SIGNATURES = {
     "harm_echo_accumulate": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP, C.c_int, C.c_int32]),
     "harm_echo_adjoint": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP, C.c_int, _VP, _VP]),
     "harm_scene_sync": (C.c_int, [_VP]),
+    "harm_batch_create": (C.c_int, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP)]),
+    "harm_batch_tune": (C.c_int, [_VP, C.POINTER(_VP)]),
+    "harm_batch_tile_rows": (C.c_int, [_VP, C.POINTER(C.c_int32)]),
+    "harm_batch_run": (C.c_int, [_VP, C.POINTER(_VP), C.c_int32]),
+    "harm_batch_destroy": (C.c_int, [_VP]),
     "harm_last_error": (C.c_char_p, []),
 }
 
@@ -251,3 +256,65 @@ def harm_echo_adjoint(scene: Scene, n0: int, np_: int, resid, grad_sigma0=None, 
 
 def harm_scene_sync(scene: Scene):
     _check(load_library().harm_scene_sync(scene.handle))
+
+
+class Batch:
+    """Owning handle of a ``harm_batch`` (keeps its scenes alive)."""
+
+    def __init__(self, ptr, scenes):
+        self._ptr = ptr
+        self.scenes = list(scenes)
+
+    @property
+    def handle(self):
+        if self._ptr is None:
+            raise HarmError(HARM_E_INVALID, "batch destroyed")
+        return self._ptr
+
+    def close(self):
+        if self._ptr is not None and _lib is not None:
+            _lib.harm_batch_destroy(self._ptr)
+        self._ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr_array(tensors, what):
+    arr = (C.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex64:
+            raise HarmError(HARM_E_INVALID, "%s[%d] must be a complex64 CUDA tensor" % (what, i))
+        if not t.is_contiguous():
+            raise HarmError(HARM_E_INVALID, "%s[%d] must be contiguous" % (what, i))
+        arr[i] = t.data_ptr()
+    return arr
+
+
+def harm_batch_create(scenes) -> Batch:
+    arr = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    out = C.c_void_p()
+    _check(load_library().harm_batch_create(arr, len(scenes), C.byref(out)))
+    return Batch(out, scenes)
+
+
+def harm_batch_tune(batch: Batch, iqs):
+    _check(load_library().harm_batch_tune(batch.handle, _ptr_array(iqs, "iq")))
+
+
+def harm_batch_tile_rows(batch: Batch):
+    rows = (C.c_int32 * len(batch.scenes))()
+    _check(load_library().harm_batch_tile_rows(batch.handle, rows))
+    return [int(v) for v in rows]
+
+
+def harm_batch_run(batch: Batch, iqs, zero_first: bool = True):
+    _check(load_library().harm_batch_run(batch.handle, _ptr_array(iqs, "iq"), 1 if zero_first else 0))
+
+
+def harm_batch_destroy(batch: Batch):
+    batch.close()
