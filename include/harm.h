@@ -196,6 +196,31 @@ harm_status harm_batch_run(harm_batch *batch, void *const *iq_dev, int32_t zero_
 /* Release the batch (waits for its stream). NULL is OK. */
 harm_status harm_batch_destroy(harm_batch *batch);
 
+/* Allocation-free batched forward run (the paper has no counterpart; this is a
+   service for callers that cannot allocate device memory where they run the
+   echo, e.g. a loop with a fixed device-memory budget or code inside a framework
+   whose caching allocator owns the device, where cudaMalloc / cudaFree could
+   synchronise the device or fail). Same result as harm_batch_create +
+   harm_batch_run over `scenes` (16-row tiles, no tuning, no graph), but the
+   launch's scratch memory -- per-scene arguments, work list, output pointers and
+   the work counter -- lives in one file-scope device array of fixed size (about
+   132 KB, held on every GPU that loads the library until the process exits), and
+   the call makes no cudaMalloc, cudaFree or other allocating call.
+   scenes[n_scenes]: mixed-precision scenes on the current device with the same
+   channel count, taps and Kaiser beta; iq_dev[n_scenes]: their complex64 IQ
+   buffers [n_channels][n_pulses][n_range] (device). zero_first = 1 clears them
+   first. Asynchronous on the first scene's stream.
+   Limits and sharing: at most 64 scenes per call (more -> HARM_E_INVALID). All
+   calls share the one array; each call rewrites it completely (including the
+   work counter, which starts at zero), but two calls whose launches overlap on
+   the GPU (different streams, no ordering between them) race on it: order such
+   calls on one stream or with events. The first call on a device looks up the
+   array's device address (cudaGetSymbolAddress); make that first call before any
+   stream capture. Errors: HARM_E_INVALID, HARM_E_UNSUPPORTED (an FP64 scene),
+   HARM_E_CUDA. */
+harm_status harm_batch_run_noalloc(harm_scene *const *scenes, int32_t n_scenes, void *const *iq_dev,
+                                   int32_t zero_first);
+
 /* Wait for the scene's stream and report device-side errors (bounded waits that
    timed out, bounds flags) raised since the last check. */
 harm_status harm_scene_sync(harm_scene *scene);

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libharm.so")
-SOURCES = ["harm_scene.cu", "harm_dispatch.cu", "harm_batch.cu", "echo_fp64.cu", "echo_mixed.cu"]
+SOURCES = ["harm_scene.cu", "harm_dispatch.cu", "harm_batch.cu", "harm_noalloc.cu", "echo_fp64.cu", "echo_mixed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -83,6 +83,7 @@ SIGNATURES = {
     "harm_batch_tile_rows": (C.c_int, [_VP, C.POINTER(C.c_int32)]),
     "harm_batch_run": (C.c_int, [_VP, C.POINTER(_VP), C.c_int32]),
     "harm_batch_destroy": (C.c_int, [_VP]),
+    "harm_batch_run_noalloc": (C.c_int, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP), C.c_int32]),
     "harm_last_error": (C.c_char_p, []),
 }
 
@@ -318,3 +319,11 @@ def harm_batch_run(batch: Batch, iqs, zero_first: bool = True):
 
 def harm_batch_destroy(batch: Batch):
     batch.close()
+
+
+def harm_batch_run_noalloc(scenes, iqs, zero_first: bool = True):
+    """Allocation-free batched run (see include/harm.h): scratch in a fixed device
+    array, at most 64 scenes per call, calls must not overlap on the GPU."""
+    arr = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
+    _check(load_library().harm_batch_run_noalloc(arr, len(scenes), _ptr_array(iqs, "iq"),
+                                                 1 if zero_first else 0))
