@@ -40,7 +40,8 @@ constexpr int NT = 256;       // threads per CTA
 constexpr int NWARP = NT / 32;
 constexpr int WT = 48;        // range bins per channel in the CTA tile
 constexpr int WT_LO = 22;     // tile window starts WT_LO bins below the reference bin
-constexpr int NBMAX = 32;     // pulses per batch
+constexpr int NBR = 32;       // pulses per chunk of FP64 tile references
+constexpr int NBG = 128;      // pulses per work item (time-Taylor window of the generator)
 constexpr int WCH = 128;      // wave components per shared-memory chunk
 constexpr int SROW = 72;      // floats per bin row of the warp buffer (2 halves of 32 + pad)
 constexpr int SHALF = 36;     // float offset of lanes 16..31 in a row
@@ -93,18 +94,24 @@ struct Layout {
     int w, tile, tx, rx, ch, pr, txd, stage, total;
 };
 
+// The wave-table chunk (generator phase) and the warp buffers (pulse loop) are
+// never live at the same time and share one region; the warp buffers are
+// cleared after the generator phase.
 __host__ __device__ inline Layout layout(int nc)
 {
     Layout L;
     int o = 0;
-    L.w = o;     o += WCH * 3 * kOrders * 8;
+    const int wbytes = WCH * 3 * kOrders * 8;
+    const int sbytes = NWARP * SBINS * SROW * 4;
+    L.w = o;
+    L.stage = o;
+    o += wbytes > sbytes ? wbytes : sbytes;
     L.tile = o;  o += 2 * nc * WT * 8;
-    L.tx = o;    o += NBMAX * (int)sizeof(AntRec);
-    L.rx = o;    o += NBMAX * nc * (int)sizeof(AntRec);
-    L.ch = o;    o += NBMAX * nc * (int)sizeof(ChanRec);
-    L.pr = o;    o += NBMAX * (int)sizeof(PulseRec);
-    L.txd = o;   o += NBMAX * 4 * 8;
-    L.stage = o; o += NWARP * SBINS * SROW * 4;
+    L.tx = o;    o += NBR * (int)sizeof(AntRec);
+    L.rx = o;    o += NBR * nc * (int)sizeof(AntRec);
+    L.ch = o;    o += NBR * nc * (int)sizeof(ChanRec);
+    L.pr = o;    o += NBR * (int)sizeof(PulseRec);
+    L.txd = o;   o += NBR * 4 * 8;
     L.total = o;
     return L;
 }
@@ -112,11 +119,11 @@ __host__ __device__ inline Layout layout(int nc)
 struct Smem {
     float2 *w;       // [WCH][3][kOrders]
     float2 *tile;    // [2][nc][WT]
-    AntRec *tx;      // [NBMAX]
-    AntRec *rx;      // [NBMAX][nc]
-    ChanRec *ch;     // [NBMAX][nc]
-    PulseRec *pr;    // [NBMAX]
-    double *txd;     // [NBMAX][4]
+    AntRec *tx;      // [NBR]
+    AntRec *rx;      // [NBR][nc]
+    ChanRec *ch;     // [NBR][nc]
+    PulseRec *pr;    // [NBR]
+    double *txd;     // [NBR][4]
     float *stage;    // [NWARP][SBINS][SROW]
 };
 
@@ -356,13 +363,18 @@ __device__ __forceinline__ void warp_scatter(float *buf, float2 *tile_c, int til
         __syncwarp();
         const int w = lane >> 1, half = lane & 1;
         const float4 *rp = reinterpret_cast<const float4 *>(buf + w * SROW + half * SHALF);
-        float ar = 0.0f, ai = 0.0f;
+        float4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = rp[q];
+        // pairwise sums: short dependency chains after the loads
+        float pr[8], pim[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            float4 v = rp[q];
-            ar += v.x + v.z;
-            ai += v.y + v.w;
+            pr[q] = v[q].x + v[q].z;
+            pim[q] = v[q].y + v[q].w;
         }
+        float ar = ((pr[0] + pr[1]) + (pr[2] + pr[3])) + ((pr[4] + pr[5]) + (pr[6] + pr[7]));
+        float ai = ((pim[0] + pim[1]) + (pim[2] + pim[3])) + ((pim[4] + pim[5]) + (pim[6] + pim[7]));
         ar += __shfl_xor_sync(FULL, ar, 1);
         ai += __shfl_xor_sync(FULL, ai, 1);
         __syncwarp();
@@ -402,6 +414,8 @@ struct FacetGeo {
     float xi_y;          // y offset from the tile reference point (exact)
     float fj;            // row offset index
     float base, cu, cv;  // NRCS base and current (cell values or uniform)
+    float base_area;     // NRCS base x facet area
+    float amp_static;    // sqrt(base x area): the amplitude factor of a static surface
     float2 z;            // speckle of the current epoch
     int epoch;           // epoch the speckle belongs to
     uint32_t fid;
@@ -512,16 +526,18 @@ __device__ __forceinline__ void facet_pulse(const Smem &sm, const MixedArgs &A, 
         const float qx = -fmaf(fmaf(xi0, R.invR, R.ux), rho_r, rt0);
         const float qy = -fmaf(fmaf(xi1, R.invR, R.uy), rho_r, rt1);
         const float qz = -fmaf(fmaf(xi2, R.invR, R.uz), rho_r, rt2);
-        float sig = G.base;
+        // sqrt(sigma0 A) with sigma0 = base (1 + m cos phi) max(0, n.Q) / (|n| Q_z):
+        // X = base A (1 + m cos phi) max(0, n.Q) / |n| = sigma0 A Q_z, so
+        // sqrt(sigma0 A) = X rsqrt(X Q_z) (one reciprocal square root)
+        float amp_s = G.amp_static;
         if (!S.static_surface) {
             float qh2 = fmaf(qx, qx, qy * qy);
             float cphi = qh2 > 0.0f ? fmaf(A.wcos, qx, A.wsin * qy) * rsqrtf(qh2) : 0.0f;
             float nq = fmaf(-sx, qx, fmaf(-sy, qy, qz));
-            float tilt = __fdividef(fmaxf(nq, 0.0f) * inv_n, qz);
-            sig = G.base * fmaf(A.wind_mod, cphi, 1.0f) * tilt;
+            float X = G.base_area * fmaf(A.wind_mod, cphi, 1.0f) * (fmaxf(nq, 0.0f) * inv_n);
+            amp_s = X > 0.0f ? X * rsqrtf(X * qz) : 0.0f;
         }
-        const float sa = sig * A.area;
-        const float amp = (sa > 0.0f ? sa * rsqrtf(sa) : 0.0f) * ampt * gr * R.ampr * rho_r;
+        const float amp = amp_s * ampt * gr * R.ampr * rho_r;
         const float vc = -fmaf(G.cu, qx, G.cv * qy);
         float phi = Q.psi + fmaf(fi, Q.ax, fmaf(G.fj, Q.ay, fmaf(Q.gam, eta, -A.k0 * (qt + qr))));
         phi = fmaf(-PR.k0t, vc, phi);
@@ -581,6 +597,8 @@ __device__ void facet_setup(const MixedArgs &A, int ix, int iy, int jref, FacetG
         }
     }
     G.base = (float)base;
+    G.base_area = (float)(base * S.area);
+    G.amp_static = (float)sqrt(base * S.area);
     G.cu = (float)cu;
     G.cv = (float)cv;
     G.epoch = -1;
@@ -623,7 +641,6 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
     const float xi_x = (float)((ix - iref) * S.dx);
     const float fi = (float)(ix - iref);
 
-    build_refs(sm, A, I.pa, I.pe, xr, yr);
     FacetGeo ga, gb;
     facet_setup(A, ix, I.ty0 + warp, jref, ga);
     facet_setup(A, ix, I.ty0 + warp + NWARP, jref, gb);
@@ -637,6 +654,9 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
             for (int o = 0; o < kOrders; ++o) ca[f][o] = cb[f][o] = 0.0f;
     }
     __syncthreads();
+    // the warp buffers share memory with the wave-table chunk: clear them
+    for (int i = threadIdx.x; i < NWARP * SBINS * SROW; i += NT) sm.stage[i] = 0.0f;
+    __syncthreads();
 
     ScatterSink<OutT> sink;
     sink.stage = sm.stage + warp * SBINS * SROW;
@@ -644,33 +664,39 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
     sink.iq = iq;
     sink.n0 = n0;
     sink.np = np;
-    for (int n = I.pa; n < I.pe; ++n) {
-        const int pi = n - I.pa;
-        const int buf = pi & 1;
-        const int e = sm.pr[pi].epoch;
-        if (e != ga.epoch) {
-            ga.z = speckle_f(S.speckle_seed, ga.fid, (uint32_t)e);
-            ga.epoch = e;
-        }
-        sink.n = n;
-        sink.buf = buf;
-        facet_pulse<TAPS>(sm, A, P, ga, ca, pi, xi_x, fi, sink);
-        if (two) {
-            if (e != gb.epoch) {
-                gb.z = speckle_f(S.speckle_seed, gb.fid, (uint32_t)e);
-                gb.epoch = e;
-            }
-            facet_pulse<TAPS>(sm, A, P, gb, cb, pi, xi_x, fi, sink);
-        }
+    for (int c0 = I.pa; c0 < I.pe; c0 += NBR) {
+        const int ce = min(c0 + NBR, I.pe);
+        __syncthreads();  // the previous chunk's flush is done with the records
+        build_refs(sm, A, c0, ce, xr, yr);
         __syncthreads();
-        for (int i = threadIdx.x; i < nc * WT; i += NT) {
-            int ch = i / WT, w = i % WT;
-            float2 *slot = sm.tile + (buf * nc + ch) * WT + w;
-            float2 v = *slot;
-            *slot = make_float2(0.f, 0.f);
-            int k = sm.ch[pi * nc + ch].kbase - WT_LO + w;
-            if ((v.x != 0.0f || v.y != 0.0f) && k >= 0 && k < S.nr)
-                gadd<OutT>(iq + 2 * ((size_t)ch * np + (n - n0)) * S.nr, (size_t)k, v.x, v.y);
+        for (int n = c0; n < ce; ++n) {
+            const int pi = n - c0;
+            const int buf = n & 1;
+            const int e = sm.pr[pi].epoch;
+            if (e != ga.epoch) {
+                ga.z = speckle_f(S.speckle_seed, ga.fid, (uint32_t)e);
+                ga.epoch = e;
+            }
+            sink.n = n;
+            sink.buf = buf;
+            facet_pulse<TAPS>(sm, A, P, ga, ca, pi, xi_x, fi, sink);
+            if (two) {
+                if (e != gb.epoch) {
+                    gb.z = speckle_f(S.speckle_seed, gb.fid, (uint32_t)e);
+                    gb.epoch = e;
+                }
+                facet_pulse<TAPS>(sm, A, P, gb, cb, pi, xi_x, fi, sink);
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < nc * WT; i += NT) {
+                int ch = i / WT, w = i % WT;
+                float2 *slot = sm.tile + (buf * nc + ch) * WT + w;
+                float2 v = *slot;
+                *slot = make_float2(0.f, 0.f);
+                int k = sm.ch[pi * nc + ch].kbase - WT_LO + w;
+                if ((v.x != 0.0f || v.y != 0.0f) && k >= 0 && k < S.nr)
+                    gadd<OutT>(iq + 2 * ((size_t)ch * np + (n - n0)) * S.nr, (size_t)k, v.x, v.y);
+            }
         }
     }
     // the other buffer was flushed one pulse earlier; make sure every thread is
@@ -821,7 +847,6 @@ __global__ void __launch_bounds__(NT, 2)
     const float xi_x = (float)((ix - iref) * S.dx);
     const float fi = (float)(ix - iref);
 
-    build_refs(sm, A, pa, pe, xr, yr);
     FacetGeo ga, gb;
     facet_setup(A, ix, ty0 + warp, jref, ga);
     facet_setup(A, ix, ty0 + warp + NWARP, jref, gb);
@@ -841,7 +866,11 @@ __global__ void __launch_bounds__(NT, 2)
     ka.np = kb.np = np;
     ka.as = ka.au = ka.av = kb.as = kb.au = kb.av = 0.0f;
     for (int n = pa; n < pe; ++n) {
-        const int pi = n - pa;
+        const int pi = (n - pa) % NBR;
+        if (pi == 0) {
+            __syncthreads();  // the previous chunk is done with the records
+            build_refs(sm, A, n, min(n + NBR, pe), xr, yr);
+        }
         __syncthreads();
         // residual window of this pulse, every channel
         for (int i = threadIdx.x; i < nc * WT; i += NT) {
@@ -1051,7 +1080,7 @@ cudaError_t launch_adjoint_mixed(const DevScene &S, const MixedTables &M, cudaSt
     return cudaSuccess;
 }
 
-int mixed_batch_pulses() { return NBMAX; }
+int mixed_batch_pulses() { return NBG; }
 
 // ---------------------------------------------------------------------------
 // Batched persistent launch (host side)

@@ -13,7 +13,7 @@ namespace harm {
 // tables of each pulse batch, plus the tap polynomials).
 constexpr int kTapDeg = 10;     // degree of each tap polynomial in t = 2f - 1
 constexpr int kSincDeg = 7;     // degree of the sinc^2 polynomial in t = 2x^2 - 1, |x| <= 1
-constexpr int kOrders = 5;      // Taylor orders in time: tau^0 .. tau^4
+constexpr int kOrders = 6;      // Taylor orders in time: tau^0 .. tau^5
 
 struct MixedTables {
     int nb = 0;             // pulses per batch (time-Taylor expansion window)
