@@ -481,6 +481,28 @@ void or_facet_states(const or_scene *s, int n, int nw, const double *kx, const d
     }
 }
 
+/* Facet states of the listed facets at pulse n: out[3][count] in list order. */
+static void list_states(const or_scene *s, int n, int nw, const double *kx, const double *ky, const double *om,
+                        const double *amp, const double *ph, int64_t count, const int64_t *facets, double *out)
+{
+    or_pulse g;
+    or_pulse_state(s, n, 0, &g);
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < count; ++q) {
+        double st[3] = {0.0, 0.0, 0.0};
+        if (!s->static_surface && nw > 0) {
+            int64_t f = facets[q];
+            int ix = (int)(f % s->nx), iy = (int)(f / s->nx);
+            double x = (ix + 0.5 - 0.5 * s->nx) * s->facet;
+            double y = (iy + 0.5 - 0.5 * s->ny) * s->facet;
+            or_surface(nw, kx, ky, om, amp, ph, x, y, g.ts, st);
+        }
+        out[q] = st[0];
+        out[count + q] = st[1];
+        out[2 * count + q] = st[2];
+    }
+}
+
 /* IQ of the listed pulses: iq[c][i][k][2] for pulse pulses[i], all channels,
    summing the facets listed in facets[0..n_fac) (all facets when facets is
    NULL). */
@@ -497,13 +519,17 @@ int or_echo(const or_scene *s, int n_list, const int *pulses, int64_t n_fac, con
         ph = malloc(sizeof(double) * nw);
         or_wave_table(s, kx, ky, om, amp, ph);
     }
-    double *st = malloc(sizeof(double) * 3 * nf);
+    int64_t nsum = facets ? n_fac : nf;
+    /* states of the summed facets only: st[3][nsum] in list order */
+    double *st = malloc(sizeof(double) * 3 * (nsum > 0 ? nsum : 1));
     double r0[OR_MAXC];
     for (int c = 0; c < nc; ++c) r0[c] = or_range_start(s, c);
-    int64_t nsum = facets ? n_fac : nf;
     for (int i = 0; i < n_list; ++i) {
         int n = pulses[i];
-        or_facet_states(s, n, nw, kx, ky, om, amp, ph, st);
+        if (facets)
+            list_states(s, n, nw, kx, ky, om, amp, ph, nsum, facets, st);
+        else
+            or_facet_states(s, n, nw, kx, ky, om, amp, ph, st);
 #pragma omp parallel for schedule(dynamic, 1)
         for (int c = 0; c < nc; ++c) {
             or_pulse g;
@@ -512,7 +538,7 @@ int or_echo(const or_scene *s, int n_list, const int *pulses, int64_t n_fac, con
             double *si = calloc(nr, sizeof(double)), *ci = calloc(nr, sizeof(double));
             for (int64_t q = 0; q < nsum; ++q) {
                 int64_t f = facets ? facets[q] : q;
-                double state[3] = {st[f], st[nf + f], st[2 * nf + f]};
+                double state[3] = {st[q], st[nsum + q], st[2 * nsum + q]};
                 double sre, sim, p;
                 contribution(s, &g, n, c, f, state, r0[c], &sre, &sim, &p);
                 spread(s, sre, sim, p, sr, cr, si, ci);

@@ -345,7 +345,7 @@ harm_status harm_scene_set_cells(harm_scene *s, int32_t ncx, int32_t ncy, double
         s->dev.cell_sigma0 = s->dev.cell_uv = nullptr;
         return HARM_OK;
     }
-    if (ncx < 1 || ncy < 1 || !(cell_m > 0) || (int64_t)ncx * ncy > (1 << 24))
+    if (ncx < 1 || ncy < 1 || !(cell_m > 0) || (int64_t)ncx * ncy > (1 << 27))
         return fail(HARM_E_INVALID, "bad cell grid %d x %d of %g m", ncx, ncy, cell_m);
     if (sigma0_dev) {
         harm_status st = check_ptr(sigma0_dev, "sigma0_dev");
