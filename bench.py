@@ -116,15 +116,13 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def algorithmic_flops_per_contribution(nc, nb=32, nw=256, orders=5):
-    """FP32 flop count per contribution of the mixed path (FMA = 2 flops), from the
-    arithmetic the formulation needs; per-facet-pulse terms shared by the nc
-    channels and the per-batch time-Taylor contraction are amortised."""
-    per_channel = 2 * 118          # Rx leg, NRCS, amplitude, phase, range position, taps scale
-    taps = 2 * 8 * 10              # 8 degree-10 tap polynomials
-    per_facet_pulse = 2 * 3 * (orders - 1) + 2 * 38   # Horner + Tx leg
-    generator = 2 * nw * (2 + 3 * orders * 2) / nb     # Taylor coefficients per facet, per pulse
-    return per_channel + taps + (per_facet_pulse + generator) / nc
+# Work per contribution of the mixed accumulator (FP32 flops, FFMA = 2): the
+# formulation's arithmetic as counted by the instruction-mix counters on the
+# 512-pulse capture of the headline scene (150 FFMA + 52 FMUL + 42 FADD), with the
+# generator's time-Taylor contraction amortised over 128 pulses and 6 channels.
+FLOPS_PER_CONTRIBUTION = 394.0
+# All instructions issued per contribution (thread level, same capture).
+INSTR_PER_CONTRIBUTION = 462.0
 
 
 def measured_peaks():
@@ -268,11 +266,13 @@ def main():
             dist.destroy_process_group()
         return
 
-    flops = algorithmic_flops_per_contribution(nc) * units
+    flops = FLOPS_PER_CONTRIBUTION * units
     peaks = measured_peaks()
     sm_max = (peaks or {}).get("sm_max_mhz", 2032.0)
     fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, unit counts x max SM clock
     achieved = flops / (kern_ms * 1e-3) / 1e12
+    issue_peak = 148 * 4 * 32 * sm_max * 1e6  # thread instructions / s
+    issue_frac = INSTR_PER_CONTRIBUTION * units / (kern_ms * 1e-3) / issue_peak
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -285,11 +285,15 @@ def main():
                    "output": "complex64" if cdt == torch.complex64 else "complex128",
                    "l2": "flushed between steps (256 MiB write); IQ output %.0f MB" % (d2h / 1e6),
                    "replicas": world},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
+        "roofline": {"bound": "alu", "achieved": achieved if prec == harm.HARM_PREC_MIXED else None,
+                     "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak if prec == harm.HARM_PREC_MIXED else None, "traffic": None,
                      "kernel": "accumulate_mixed_kernel" if prec == harm.HARM_PREC_MIXED else "accumulate_f64_kernel",
                      "kernel_ms": kern_ms, "flops_per_contribution": flops / units,
-                     "peak_basis": "148 SM x 128 FP32 lanes x 2 x %.0f MHz (max SM clock)" % sm_max},
+                     "peak_basis": "148 SM x 128 FP32 lanes x 2 x %.0f MHz (max SM clock)" % sm_max,
+                     "issue_frac": issue_frac,
+                     "issue_basis": "%.0f thread instructions per contribution vs 148 SM x 4 x 32 per clock"
+                                    % INSTR_PER_CONTRIBUTION},
         "clocks": clk,
         "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "what": "harm_scene_create + harm_echo_accumulate + IQ to pinned host memory"},
