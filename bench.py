@@ -125,6 +125,22 @@ FLOPS_PER_CONTRIBUTION = 394.0
 INSTR_PER_CONTRIBUTION = 462.0
 
 
+def max_over_ranks(total_ms, dist=None, device="cpu"):
+    """Slowest rank's timed total (ms): the replicas' common clock."""
+    if dist is None:
+        return float(total_ms)
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, units_per_rank, steps, total_ms):
+    """Whole-job throughput of `world` independent replicas: all ranks' units over
+    the slowest rank's time."""
+    return world * units_per_rank * steps / (total_ms * 1e-3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -226,12 +242,8 @@ def main():
     clk = clocks.stop()
     harm.harm_scene_sync(scene)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    t_max = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = float(t_max.item())
-    value = world * units * args.steps / (total_ms * 1e-3)
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
+    value = replica_value(world, units, args.steps, total_ms)
 
     # -- roofline of the accumulator kernel alone (no memset), same stream
     kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
