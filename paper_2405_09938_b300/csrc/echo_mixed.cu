@@ -70,6 +70,24 @@ struct __align__(16) PulseRec {
     int pad;
 };
 
+// The same references with every value duplicated into a pair (v, v): the
+// forward path evaluates two facets per thread with packed FP32x2 arithmetic and
+// reads each reference as one 64-bit operand.
+struct __align__(16) AntRec2 {
+    float2 ux, uy, uz, invR;
+    float2 inv2R, inv2R2, u0, v0;
+    float2 aRx, aRy, aRz, ampr;
+    float2 eRx, eRy, eRz, pad;
+};
+
+struct __align__(16) ChanRec2 {
+    float2 psi, ax, ay, gam;
+    float2 pfrac;
+    int kbase;
+    int pad0;
+    float2 pad1;
+};
+
 struct MixedArgs {
     DevScene S;
     const float2 *ex, *ey, *wt;
@@ -84,9 +102,11 @@ struct MixedArgs {
 // Polynomial tables shared by every scene of a launch (they depend only on the
 // Kaiser beta): passed as kernel parameters so the inner loops read them from
 // the constant bank.
+// Each coefficient is stored as the pair (c, c) so that the packed two-facet
+// evaluation reads it as one 64-bit constant operand; scalar code reads .x.
 struct PolyArgs {
-    float tap[8][kTapDeg + 1];
-    float sinc2[kSincDeg + 1];
+    float2 tap[8][kTapDeg + 1];
+    float2 sinc2[kSincDeg + 1];
 };
 
 // Shared-memory layout (bytes), sized for nc channels.
@@ -97,7 +117,7 @@ struct Layout {
 // The wave-table chunk (generator phase) and the warp buffers (pulse loop) are
 // never live at the same time and share one region; the warp buffers are
 // cleared after the generator phase.
-__host__ __device__ inline Layout layout(int nc)
+__host__ __device__ inline Layout layout(int nc, bool dup)
 {
     Layout L;
     int o = 0;
@@ -107,9 +127,9 @@ __host__ __device__ inline Layout layout(int nc)
     L.stage = o;
     o += wbytes > sbytes ? wbytes : sbytes;
     L.tile = o;  o += 2 * nc * WT * 8;
-    L.tx = o;    o += NBR * (int)sizeof(AntRec);
-    L.rx = o;    o += NBR * nc * (int)sizeof(AntRec);
-    L.ch = o;    o += NBR * nc * (int)sizeof(ChanRec);
+    L.tx = o;    o += NBR * (int)(dup ? sizeof(AntRec2) : sizeof(AntRec));
+    L.rx = o;    o += NBR * nc * (int)(dup ? sizeof(AntRec2) : sizeof(AntRec));
+    L.ch = o;    o += NBR * nc * (int)(dup ? sizeof(ChanRec2) : sizeof(ChanRec));
     L.pr = o;    o += NBR * (int)sizeof(PulseRec);
     L.txd = o;   o += NBR * 4 * 8;
     L.total = o;
@@ -119,23 +139,29 @@ __host__ __device__ inline Layout layout(int nc)
 struct Smem {
     float2 *w;       // [WCH][3][kOrders]
     float2 *tile;    // [2][nc][WT]
-    AntRec *tx;      // [NBR]
+    AntRec *tx;      // [NBR]          (scalar layout: adjoint)
     AntRec *rx;      // [NBR][nc]
     ChanRec *ch;     // [NBR][nc]
+    AntRec2 *tx2;    // [NBR]          (pair layout: forward, same memory)
+    AntRec2 *rx2;    // [NBR][nc]
+    ChanRec2 *ch2;   // [NBR][nc]
     PulseRec *pr;    // [NBR]
     double *txd;     // [NBR][4]
     float *stage;    // [NWARP][SBINS][SROW]
 };
 
-__device__ __forceinline__ Smem carve(unsigned char *raw, int nc)
+__device__ __forceinline__ Smem carve(unsigned char *raw, int nc, bool dup)
 {
-    Layout L = layout(nc);
+    Layout L = layout(nc, dup);
     Smem s;
     s.w = reinterpret_cast<float2 *>(raw + L.w);
     s.tile = reinterpret_cast<float2 *>(raw + L.tile);
     s.tx = reinterpret_cast<AntRec *>(raw + L.tx);
     s.rx = reinterpret_cast<AntRec *>(raw + L.rx);
     s.ch = reinterpret_cast<ChanRec *>(raw + L.ch);
+    s.tx2 = reinterpret_cast<AntRec2 *>(raw + L.tx);
+    s.rx2 = reinterpret_cast<AntRec2 *>(raw + L.rx);
+    s.ch2 = reinterpret_cast<ChanRec2 *>(raw + L.ch);
     s.pr = reinterpret_cast<PulseRec *>(raw + L.pr);
     s.txd = reinterpret_cast<double *>(raw + L.txd);
     s.stage = reinterpret_cast<float *>(raw + L.stage);
@@ -149,13 +175,34 @@ __device__ __forceinline__ float sinc2f(const PolyArgs &P, float x)
     float u = x * x;
     if (u <= 1.0f) {
         float t = fmaf(2.0f, u, -1.0f);
-        float r = P.sinc2[kSincDeg];
+        float r = P.sinc2[kSincDeg].x;
 #pragma unroll
-        for (int d = kSincDeg - 1; d >= 0; --d) r = fmaf(r, t, P.sinc2[d]);
+        for (int d = kSincDeg - 1; d >= 0; --d) r = fmaf(r, t, P.sinc2[d].x);
         return r;
     }
     float s = __fdividef(sinpif(x), kPiF * x);
     return s * s;
+}
+
+// Packed FP32x2 arithmetic (two facets per thread: .x and .y).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+
+// sinc^2 of two arguments: the packed polynomial when both are within |x| <= 1.
+__device__ __forceinline__ float2 sinc2_2(const PolyArgs &P, float2 x)
+{
+    const float2 u = mul2(x, x);
+    if (u.x <= 1.0f && u.y <= 1.0f) {
+        const float2 t = fma2(make_float2(2.0f, 2.0f), u, make_float2(-1.0f, -1.0f));
+        float2 r = P.sinc2[kSincDeg];
+#pragma unroll
+        for (int d = kSincDeg - 1; d >= 0; --d) r = fma2(r, t, P.sinc2[d]);
+        return r;
+    }
+    return make_float2(sinc2f(P, x.x), sinc2f(P, x.y));
 }
 
 __device__ __forceinline__ double wrap_pi(double a)
@@ -201,9 +248,22 @@ __device__ void tile_ref(const AntState &A, double xr, double yr, double u[3], d
     o.pad = 0.0f;
 }
 
+__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ AntRec2 dup_rec(const AntRec &r)
+{
+    AntRec2 o;
+    o.ux = dup(r.ux); o.uy = dup(r.uy); o.uz = dup(r.uz); o.invR = dup(r.invR);
+    o.inv2R = dup(r.inv2R); o.inv2R2 = dup(r.inv2R2); o.u0 = dup(r.u0); o.v0 = dup(r.v0);
+    o.aRx = dup(r.aRx); o.aRy = dup(r.aRy); o.aRz = dup(r.aRz); o.ampr = dup(r.ampr);
+    o.eRx = dup(r.eRx); o.eRy = dup(r.eRy); o.eRz = dup(r.eRz); o.pad = dup(0.0f);
+    return o;
+}
+
 // FP64 references of the batch's pulses [pa, pe) for the tile reference point
 // (xr, yr); thread-parallel over (pulse, antenna), one barrier between the
-// transmit and receive stages.
+// transmit and receive stages. DUP selects the pair layout of the forward path.
+template <bool DUP>
 __device__ void build_refs(const Smem &sm, const MixedArgs &A, int pa, int pe, double xr, double yr)
 {
     const DevScene &S = A.S;
@@ -212,7 +272,12 @@ __device__ void build_refs(const Smem &sm, const MixedArgs &A, int pa, int pe, d
         int n = pa + t;
         const PulseState &P = S.pulses[n];
         double u[3], dref;
-        tile_ref(P.tx, xr, yr, u, dref, sm.tx[t]);
+        AntRec r;
+        tile_ref(P.tx, xr, yr, u, dref, r);
+        if (DUP)
+            sm.tx2[t] = dup_rec(r);
+        else
+            sm.tx[t] = r;
         sm.txd[4 * t + 0] = u[0];
         sm.txd[4 * t + 1] = u[1];
         sm.txd[4 * t + 2] = u[2];
@@ -230,7 +295,8 @@ __device__ void build_refs(const Smem &sm, const MixedArgs &A, int pa, int pe, d
         int n = pa + pi;
         const RxState &Rs = S.rx[(size_t)n * S.nc + c];
         double u[3], dref;
-        tile_ref(Rs.rx, xr, yr, u, dref, sm.rx[t]);
+        AntRec r;
+        tile_ref(Rs.rx, xr, yr, u, dref, r);
         const double *td = sm.txd + 4 * pi;
         double off = td[3] + dref;  // (R_t + R_r) - (Rbar_t + Rbar_r)
         ChanRec q;
@@ -243,7 +309,22 @@ __device__ void build_refs(const Smem &sm, const MixedArgs &A, int pa, int pe, d
         q.kbase = (int)kb;
         q.pfrac = (float)(p - kb);
         q.pad0 = q.pad1 = 0.0f;
-        sm.ch[t] = q;
+        if (DUP) {
+            sm.rx2[t] = dup_rec(r);
+            ChanRec2 q2;
+            q2.psi = dup(q.psi);
+            q2.ax = dup(q.ax);
+            q2.ay = dup(q.ay);
+            q2.gam = dup(q.gam);
+            q2.pfrac = dup(q.pfrac);
+            q2.kbase = q.kbase;
+            q2.pad0 = 0;
+            q2.pad1 = dup(0.0f);
+            sm.ch2[t] = q2;
+        } else {
+            sm.rx[t] = r;
+            sm.ch[t] = q;
+        }
     }
 }
 
@@ -336,12 +417,14 @@ __device__ __forceinline__ void gadd1(OutT *iq, size_t idx, int comp, float v)
 
 // Warp pre-reduction of the lanes' 8 complex taps at bins kb .. kb + 7 into a
 // 16-bin window. Each lane writes its taps into its own column of the warp
-// buffer (rows = bins relative to the warp's lowest bin; the buffer is all
-// zero between calls), then lane (w, half) sums half of bin row w with vector
-// loads, the halves combine by one shuffle, and one shared atomic per
-// (bin, component) adds the window to the CTA range tile (a global atomic
-// outside it). Lanes whose bins spread over more than 8 bins fall back to
-// direct atomics.
+// buffer (rows = bins relative to the warp's lowest bin; the buffer is all zero
+// between calls); within a row the lane's column is rotated by 4 x row so that
+// the 16 lanes of a half-warp always store to 16 distinct bank pairs whatever
+// their rows. Lane (w, half) then sums half of bin row w with vector loads (rows
+// beyond the warp's span are skipped), the halves combine by one shuffle, and one
+// shared atomic per (bin, component) adds the window to the CTA range tile (a
+// global atomic outside it). Lanes whose bins spread over more than 8 bins fall
+// back to direct atomics.
 template <typename OutT>
 __device__ __forceinline__ void warp_scatter(float *buf, float2 *tile_c, int tile_base, int kb, bool valid,
                                              const float h[8], float sr, float si, int nr, OutT *grow,
@@ -353,34 +436,42 @@ __device__ __forceinline__ void warp_scatter(float *buf, float2 *tile_c, int til
     if (kmin == INT_MAX) return;
     const int kmax = __reduce_max_sync(FULL, valid ? kb : INT_MIN);
     if (kmax - kmin <= SBINS - 8) {
-        float *col = buf + (lane < 16 ? 2 * lane : SHALF + 2 * (lane - 16));
         const int o = kb - kmin;
+        const int ll = lane & 15;
+        const int hb = lane < 16 ? 0 : SHALF;
+        const int rot = (ll - 4 * o) & 15;
+        // column of row o + j is hb + 2 ((rot - 4 j) & 15): four distinct values
+        float *col[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) col[m] = buf + hb + 2 * ((rot - 4 * m) & 15) + o * SROW;
         if (valid) {
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                *reinterpret_cast<float2 *>(col + (o + j) * SROW) = make_float2(h[j] * sr, h[j] * si);
+                *reinterpret_cast<float2 *>(col[j & 3] + j * SROW) = make_float2(h[j] * sr, h[j] * si);
         }
         __syncwarp();
         const int w = lane >> 1, half = lane & 1;
-        const float4 *rp = reinterpret_cast<const float4 *>(buf + w * SROW + half * SHALF);
-        float4 v[8];
+        float ar = 0.0f, ai = 0.0f;
+        if (w < kmax - kmin + 8) {
+            const float4 *rp = reinterpret_cast<const float4 *>(buf + w * SROW + half * SHALF);
+            float4 v[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = rp[q];
-        // pairwise sums: short dependency chains after the loads
-        float pr[8], pim[8];
+            for (int q = 0; q < 8; ++q) v[q] = rp[q];
+            // packed (re, im) pairwise sums: short dependency chains after the loads
+            float2 c[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            pr[q] = v[q].x + v[q].z;
-            pim[q] = v[q].y + v[q].w;
+            for (int q = 0; q < 8; ++q) c[q] = add2(make_float2(v[q].x, v[q].y), make_float2(v[q].z, v[q].w));
+            const float2 sum =
+                add2(add2(add2(c[0], c[1]), add2(c[2], c[3])), add2(add2(c[4], c[5]), add2(c[6], c[7])));
+            ar = sum.x;
+            ai = sum.y;
         }
-        float ar = ((pr[0] + pr[1]) + (pr[2] + pr[3])) + ((pr[4] + pr[5]) + (pr[6] + pr[7]));
-        float ai = ((pim[0] + pim[1]) + (pim[2] + pim[3])) + ((pim[4] + pim[5]) + (pim[6] + pim[7]));
         ar += __shfl_xor_sync(FULL, ar, 1);
         ai += __shfl_xor_sync(FULL, ai, 1);
         __syncwarp();
         if (valid) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) *reinterpret_cast<float2 *>(col + (o + j) * SROW) = make_float2(0.f, 0.f);
+            for (int j = 0; j < 8; ++j) *reinterpret_cast<float2 *>(col[j & 3] + j * SROW) = make_float2(0.f, 0.f);
         }
         const float val = half ? ai : ar;
         const int k = kmin + w;
@@ -562,13 +653,142 @@ __device__ __forceinline__ void facet_pulse(const Smem &sm, const MixedArgs &A, 
             const float t = fmaf(2.0f, fr, -1.0f);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                float v = P.tap[j][kTapDeg];
+                float v = P.tap[j][kTapDeg].x;
 #pragma unroll
-                for (int d = kTapDeg - 1; d >= 0; --d) v = fmaf(v, t, P.tap[j][d]);
+                for (int d = kTapDeg - 1; d >= 0; --d) v = fmaf(v, t, P.tap[j][d].x);
                 h[j] = v;
             }
         }
         sink(A, ch, Q, kb, h, vre, vim, qx, qy, PR.k0t, G.valid);
+    }
+}
+
+// Per-thread pair of facets (same column, rows w and w + 8) for the packed path.
+struct PairGeo {
+    float2 xi_y, fj, base_area, amp_static, cu, cv, zr, zi;
+    bool va, vb;
+};
+
+__device__ __forceinline__ float2 horner2(const float2 c[kOrders], float2 t)
+{
+    float2 r = c[kOrders - 1];
+#pragma unroll
+    for (int o = kOrders - 2; o >= 0; --o) r = fma2(r, t, c[o]);
+    return r;
+}
+
+// Forward contribution of the thread's two facets for pulse pi (chunk index),
+// every channel: the same arithmetic as facet_pulse, on FP32x2 pairs (facet a in
+// .x, facet b in .y); transcendentals and integer work per element.
+template <int TAPS, typename OutT>
+__device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A, const PolyArgs &P, const PairGeo &G,
+                                             const float2 C[3][kOrders], int pi, float xi_x, float fi,
+                                             ScatterSink<OutT> &sink)
+{
+    const DevScene &S = A.S;
+    const int nc = S.nc;
+    const float2 one = make_float2(1.0f, 1.0f);
+    const PulseRec PR = sm.pr[pi];
+    const float2 tau = dup(PR.tau);
+    const float2 eta = horner2(C[0], tau);
+    const float2 sx = horner2(C[1], tau);
+    const float2 sy = horner2(C[2], tau);
+    const float2 X0 = dup(xi_x), X1 = G.xi_y;
+    const float2 b2 = fma2(X0, X0, fma2(X1, X1, mul2(eta, eta)));
+    const float2 nn = fma2(sx, sx, fma2(sy, sy, one));
+    const float2 inv_n = make_float2(rsqrtf(nn.x), rsqrtf(nn.y));
+
+    // transmit leg (shared by the channels)
+    const AntRec2 T = sm.tx2[pi];
+    const float2 at = fma2(T.ux, X0, fma2(T.uy, X1, mul2(T.uz, eta)));
+    const float2 st = fma2(neg2(at), at, b2);
+    const float2 qt = mul2(st, fma2(neg2(at), T.inv2R2, T.inv2R));
+    const float2 dt = add2(at, qt);
+    const float2 et = mul2(dt, T.invR);
+    const float2 rho_t = fma2(et, et, sub2(one, et));
+    const float2 ut = mul2(add2(T.u0, fma2(X0, T.aRx, fma2(X1, T.aRy, mul2(eta, T.aRz)))), rho_t);
+    const float2 vt = mul2(add2(T.v0, fma2(X0, T.eRx, fma2(X1, T.eRy, mul2(eta, T.eRz)))), rho_t);
+    const float2 gt = mul2(sinc2_2(P, mul2(dup(A.tx_laz_l), ut)), sinc2_2(P, mul2(dup(A.tx_lel_l), vt)));
+    const float2 rt0 = mul2(fma2(X0, T.invR, T.ux), rho_t);
+    const float2 rt1 = mul2(fma2(X1, T.invR, T.uy), rho_t);
+    const float2 rt2 = mul2(fma2(eta, T.invR, T.uz), rho_t);
+    const float2 ampt = mul2(mul2(gt, T.ampr), rho_t);
+
+    const AntRec2 *RX = sm.rx2 + pi * nc;
+    const ChanRec2 *CH = sm.ch2 + pi * nc;
+    for (int ch = 0; ch < nc; ++ch) {
+        const AntRec2 R = RX[ch];
+        const ChanRec2 Q = CH[ch];
+        const float2 ar = fma2(R.ux, X0, fma2(R.uy, X1, mul2(R.uz, eta)));
+        const float2 sr_ = fma2(neg2(ar), ar, b2);
+        const float2 qr = mul2(sr_, fma2(neg2(ar), R.inv2R2, R.inv2R));
+        const float2 dr = add2(ar, qr);
+        const float2 er = mul2(dr, R.invR);
+        const float2 rho_r = fma2(er, er, sub2(one, er));
+        const float2 ur = mul2(add2(R.u0, fma2(X0, R.aRx, fma2(X1, R.aRy, mul2(eta, R.aRz)))), rho_r);
+        const float2 vr = mul2(add2(R.v0, fma2(X0, R.eRx, fma2(X1, R.eRy, mul2(eta, R.eRz)))), rho_r);
+        const float2 gr = mul2(sinc2_2(P, mul2(dup(A.rx_laz_l[ch]), ur)), sinc2_2(P, mul2(dup(A.rx_lel_l[ch]), vr)));
+        const float2 qx = neg2(fma2(fma2(X0, R.invR, R.ux), rho_r, rt0));
+        const float2 qy = neg2(fma2(fma2(X1, R.invR, R.uy), rho_r, rt1));
+        const float2 qz = neg2(fma2(fma2(eta, R.invR, R.uz), rho_r, rt2));
+        // sqrt(sigma0 A) = X rsqrt(X Q_z), X = base A (1 + m cos phi) max(0, n.Q) / |n|
+        float2 amp_s = G.amp_static;
+        if (!S.static_surface) {
+            const float2 qh2 = fma2(qx, qx, mul2(qy, qy));
+            const float2 rq = make_float2(qh2.x > 0.0f ? rsqrtf(qh2.x) : 0.0f, qh2.y > 0.0f ? rsqrtf(qh2.y) : 0.0f);
+            const float2 cphi = mul2(fma2(dup(A.wcos), qx, mul2(dup(A.wsin), qy)), rq);
+            const float2 nq = fma2(neg2(sx), qx, fma2(neg2(sy), qy, qz));
+            const float2 nqp = make_float2(fmaxf(nq.x, 0.0f), fmaxf(nq.y, 0.0f));
+            const float2 X = mul2(mul2(G.base_area, fma2(dup(A.wind_mod), cphi, one)), mul2(nqp, inv_n));
+            const float2 Xq = mul2(X, qz);
+            amp_s = make_float2(X.x > 0.0f ? X.x * rsqrtf(Xq.x) : 0.0f, X.y > 0.0f ? X.y * rsqrtf(Xq.y) : 0.0f);
+        }
+        const float2 amp = mul2(mul2(mul2(amp_s, ampt), mul2(gr, R.ampr)), rho_r);
+        const float2 vc = neg2(fma2(G.cu, qx, mul2(G.cv, qy)));
+        float2 phi = fma2(dup(fi), Q.ax, Q.psi);
+        phi = fma2(G.fj, Q.ay, phi);
+        phi = fma2(Q.gam, eta, phi);
+        phi = fma2(dup(-A.k0), add2(qt, qr), phi);
+        phi = fma2(dup(-PR.k0t), vc, phi);
+        const float2 kk = make_float2(rintf(phi.x * 0.15915494309189535f), rintf(phi.y * 0.15915494309189535f));
+        phi = fma2(neg2(kk), dup(6.28125f), phi);
+        phi = fma2(neg2(kk), dup(1.9353071795864769e-3f), phi);
+        float sa, ca, sb, cb;
+        __sincosf(phi.x, &sa, &ca);
+        __sincosf(phi.y, &sb, &cb);
+        const float2 sp = make_float2(sa, sb), cp = make_float2(ca, cb);
+        const float2 zr = mul2(amp, G.zr), zi = mul2(amp, G.zi);
+        const float2 vre = fma2(zr, cp, neg2(mul2(zi, sp)));
+        const float2 vim = fma2(zr, sp, mul2(zi, cp));
+        const float2 p = fma2(add2(dt, dr), dup(A.inv_dr), Q.pfrac);
+        const float2 kf = make_float2(floorf(p.x), floorf(p.y));
+        const float2 fr = sub2(p, kf);
+        int kba, kbb;
+        float ha[8], hb[8];
+        if (TAPS == 1) {
+            kba = Q.kbase + (int)kf.x;
+            kbb = Q.kbase + (int)kf.y;
+            ha[0] = hb[0] = 1.0f;
+#pragma unroll
+            for (int j = 1; j < 8; ++j) ha[j] = hb[j] = 0.0f;
+        } else {
+            kba = Q.kbase + (int)kf.x - 3;
+            kbb = Q.kbase + (int)kf.y - 3;
+            const float2 t = fma2(dup(2.0f), fr, dup(-1.0f));
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float2 v = P.tap[j][kTapDeg];
+#pragma unroll
+                for (int d = kTapDeg - 1; d >= 0; --d) v = fma2(v, t, P.tap[j][d]);
+                ha[j] = v.x;
+                hb[j] = v.y;
+            }
+        }
+        float2 *tile_c = sink.tiles + (sink.buf * nc + ch) * WT;
+        const int tile_base = Q.kbase - WT_LO;
+        OutT *grow = sink.iq + 2 * ((size_t)ch * sink.np + (sink.n - sink.n0)) * S.nr;
+        warp_scatter<OutT>(sink.stage, tile_c, tile_base, kba, G.va, ha, vre.x, vim.x, S.nr, grow, S.flags);
+        warp_scatter<OutT>(sink.stage, tile_c, tile_base, kbb, G.vb, hb, vre.y, vim.y, S.nr, grow, S.flags);
     }
 }
 
@@ -664,10 +884,26 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
     sink.iq = iq;
     sink.n0 = n0;
     sink.np = np;
+    // pack the two facets: .x = row w, .y = row w + 8 (a copy of .x, masked off, for 8-row tiles)
+    PairGeo G;
+    const FacetGeo &gq = two ? gb : ga;
+    G.xi_y = make_float2(ga.xi_y, gq.xi_y);
+    G.fj = make_float2(ga.fj, gq.fj);
+    G.base_area = make_float2(ga.base_area, gq.base_area);
+    G.amp_static = make_float2(ga.amp_static, gq.amp_static);
+    G.cu = make_float2(ga.cu, gq.cu);
+    G.cv = make_float2(ga.cv, gq.cv);
+    G.va = ga.valid;
+    G.vb = two && gb.valid;
+    float2 C[3][kOrders];
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int o = 0; o < kOrders; ++o) C[f][o] = make_float2(ca[f][o], two ? cb[f][o] : ca[f][o]);
     for (int c0 = I.pa; c0 < I.pe; c0 += NBR) {
         const int ce = min(c0 + NBR, I.pe);
         __syncthreads();  // the previous chunk's flush is done with the records
-        build_refs(sm, A, c0, ce, xr, yr);
+        build_refs<true>(sm, A, c0, ce, xr, yr);
         __syncthreads();
         for (int n = c0; n < ce; ++n) {
             const int pi = n - c0;
@@ -677,23 +913,22 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
                 ga.z = speckle_f(S.speckle_seed, ga.fid, (uint32_t)e);
                 ga.epoch = e;
             }
+            if (two && e != gb.epoch) {
+                gb.z = speckle_f(S.speckle_seed, gb.fid, (uint32_t)e);
+                gb.epoch = e;
+            }
+            G.zr = make_float2(ga.z.x, two ? gb.z.x : 0.0f);
+            G.zi = make_float2(ga.z.y, two ? gb.z.y : 0.0f);
             sink.n = n;
             sink.buf = buf;
-            facet_pulse<TAPS>(sm, A, P, ga, ca, pi, xi_x, fi, sink);
-            if (two) {
-                if (e != gb.epoch) {
-                    gb.z = speckle_f(S.speckle_seed, gb.fid, (uint32_t)e);
-                    gb.epoch = e;
-                }
-                facet_pulse<TAPS>(sm, A, P, gb, cb, pi, xi_x, fi, sink);
-            }
+            facet_pulse2<TAPS, OutT>(sm, A, P, G, C, pi, xi_x, fi, sink);
             __syncthreads();
             for (int i = threadIdx.x; i < nc * WT; i += NT) {
                 int ch = i / WT, w = i % WT;
                 float2 *slot = sm.tile + (buf * nc + ch) * WT + w;
                 float2 v = *slot;
                 *slot = make_float2(0.f, 0.f);
-                int k = sm.ch[pi * nc + ch].kbase - WT_LO + w;
+                int k = sm.ch2[pi * nc + ch].kbase - WT_LO + w;
                 if ((v.x != 0.0f || v.y != 0.0f) && k >= 0 && k < S.nr)
                     gadd<OutT>(iq + 2 * ((size_t)ch * np + (n - n0)) * S.nr, (size_t)k, v.x, v.y);
             }
@@ -715,7 +950,7 @@ __global__ void __launch_bounds__(NT, 2)
     accumulate_mixed_kernel(MixedArgs A, PolyArgs P, int n0, int np, int b0, int ty, OutT *iq)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Smem sm = carve(smem_raw, A.S.nc);
+    const Smem sm = carve(smem_raw, A.S.nc, true);
     const ItemGeo I = item_geo(A, blockIdx.x, b0 + blockIdx.y, ty, n0, np);
     if (I.pa >= I.pe) return;
     clear_smem(sm, A.S.nc);
@@ -746,7 +981,7 @@ __global__ void __launch_bounds__(NT, 2) batch_mixed_kernel(BatchItems B, PolyAr
     __shared__ MixedArgs args;
     __shared__ int s_item, s_scene;
     const int nc_max = B.args[0].S.nc;  // layout sized for the first scene's channels (all equal)
-    const Smem sm = carve(smem_raw, nc_max);
+    const Smem sm = carve(smem_raw, nc_max, true);
     int cur_scene = -1;
     clear_smem(sm, nc_max);
     for (;;) {
@@ -831,7 +1066,7 @@ __global__ void __launch_bounds__(NT, 2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DevScene &S = A.S;
     const int nc = S.nc;
-    const Smem sm = carve(smem_raw, nc);
+    const Smem sm = carve(smem_raw, nc, false);
     const int tiles_x = (S.nx + TX - 1) / TX;
     const int tx0 = (blockIdx.x % tiles_x) * TX;
     const int ty0 = (blockIdx.x / tiles_x) * TY;
@@ -869,7 +1104,7 @@ __global__ void __launch_bounds__(NT, 2)
         const int pi = (n - pa) % NBR;
         if (pi == 0) {
             __syncthreads();  // the previous chunk is done with the records
-            build_refs(sm, A, n, min(n + NBR, pe), xr, yr);
+            build_refs<false>(sm, A, n, min(n + NBR, pe), xr, yr);
         }
         __syncthreads();
         // residual window of this pulse, every channel
@@ -906,7 +1141,7 @@ __global__ void __launch_bounds__(NT, 2) generate_mixed_kernel(MixedArgs A, int 
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DevScene &S = A.S;
-    const Smem sm = carve(smem_raw, S.nc);
+    const Smem sm = carve(smem_raw, S.nc, false);
     const int tiles_x = (S.nx + TX - 1) / TX;
     const int tx0 = (blockIdx.x % tiles_x) * TX;
     const int ty0 = (blockIdx.x / tiles_x) * TY;
@@ -975,8 +1210,8 @@ PolyArgs make_poly(const MixedTables &M)
 {
     PolyArgs P;
     for (int j = 0; j < 8; ++j)
-        for (int d = 0; d <= kTapDeg; ++d) P.tap[j][d] = M.tap[j][d];
-    for (int d = 0; d <= kSincDeg; ++d) P.sinc2[d] = M.sinc2[d];
+        for (int d = 0; d <= kTapDeg; ++d) P.tap[j][d] = make_float2(M.tap[j][d], M.tap[j][d]);
+    for (int d = 0; d <= kSincDeg; ++d) P.sinc2[d] = make_float2(M.sinc2[d], M.sinc2[d]);
     return P;
 }
 
@@ -988,13 +1223,13 @@ cudaError_t prep(K kernel, int bytes)
 
 }  // namespace
 
-int mixed_smem_bytes(int nc) { return layout(nc).total; }
+int mixed_smem_bytes(int nc) { return layout(nc, true).total; }
 
 cudaError_t launch_generate_mixed(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np,
                                   float *state)
 {
     MixedArgs A = make_args(S, M);
-    const int bytes = layout(S.nc).total;
+    const int bytes = layout(S.nc, false).total;
     cudaError_t e = prep(generate_mixed_kernel, bytes);
     if (e != cudaSuccess) return e;
     int tiles = ((S.nx + TX - 1) / TX) * ((S.ny + TY - 1) / TY);
@@ -1012,7 +1247,7 @@ cudaError_t launch_accumulate_mixed(const DevScene &S, const MixedTables &M, cud
 {
     MixedArgs A = make_args(S, M);
     PolyArgs P = make_poly(M);
-    const int bytes = layout(S.nc).total;
+    const int bytes = layout(S.nc, true).total;
     const int ty = TY;
     int tiles = ((S.nx + TX - 1) / TX) * ((S.ny + ty - 1) / ty);
     int b0 = n0 / M.nb, b1 = (n0 + np - 1) / M.nb;
@@ -1047,7 +1282,7 @@ cudaError_t launch_adjoint_mixed(const DevScene &S, const MixedTables &M, cudaSt
 {
     MixedArgs A = make_args(S, M);
     PolyArgs P = make_poly(M);
-    const int bytes = layout(S.nc).total;
+    const int bytes = layout(S.nc, false).total;
     int tiles = ((S.nx + TX - 1) / TX) * ((S.ny + TY - 1) / TY);
     int b0 = n0 / M.nb, b1 = (n0 + np - 1) / M.nb;
     cudaError_t e;
@@ -1117,7 +1352,7 @@ cudaError_t batch_launch(const BatchLaunch &L, cudaStream_t st)
     B.n = L.n;
     B.total = L.total;
     PolyArgs P = make_poly(*L.poly);
-    const int bytes = layout(L.nc).total;
+    const int bytes = layout(L.nc, true).total;
     cudaError_t e;
     if (L.taps == 1) {
         if ((e = prep(batch_mixed_kernel<1>, bytes)) != cudaSuccess) return e;
