@@ -2,26 +2,29 @@
 // reference bistatic range and each tile's range offset; FP32 for the per-facet
 // geometry, antenna patterns, NRCS, phase, interpolation taps and accumulation.
 //
-// Work decomposition (one CTA = a 32 x 16 facet tile x one batch of pulses):
-//  1. FP64 tile references: for every pulse of the batch and every antenna, the
+// Work decomposition (one CTA = a 32 x 16 facet tile x a 128-pulse batch):
+//  1. Facet generator: the surface of the tile over the batch is expanded in time
+//     about the batch centre, eta(t_c + tau) = sum_m eta_m tau^m (m <= 5), with
+//     the Taylor coefficients eta_m = Re sum_w Q_w E_{w,m} accumulated over the
+//     wave components (register-blocked FP32 contraction, separable phasors Q).
+//  2. FP64 tile references, per 32-pulse chunk: for every pulse and antenna, the
 //     range R from the antenna to the tile's reference point on the mean surface,
 //     its unit vector and the tile's reduced reference phase and range-bin offset.
-//     Per facet, r - R is then a small offset that FP32 carries to ~1e-8 m:
+//     Per facet, r - R is a small offset that FP32 carries to ~1e-8 m:
 //        r - R = a + (b - a^2) / (2R) + (a^3 - a b) / (2R^2),  a = u.xi, b = |xi|^2
 //     for the facet offset xi from the reference point; the linear phase term
 //     K0 (u_t + u_r).xi is split into exactly-reduced lattice steps.
-//  2. Facet generator: the surface of the tile over the batch is expanded in time
-//     about the batch centre, eta(t_c + tau) = sum_m eta_m tau^m, with the
-//     Taylor coefficients eta_m = Re sum_w Q_w E_{w,m} accumulated over the wave
-//     components (register-blocked FP32 contraction, separable phasors Q).
-//  3. For each pulse: Horner gives (eta, eta_x, eta_y); each facet forms its
-//     contribution for every channel (Eq. 3, 4, 16) and its 8 Kaiser-sinc taps
+//  3. For each pulse: each thread evaluates its two facets (rows w and w + 8 of
+//     the tile) together in packed FP32x2 arithmetic: Horner in time, then per
+//     channel the contribution (Eq. 3, 4, 16) and its 8 Kaiser-sinc taps
 //     (polynomials in the fractional bin). The warp pre-reduces its 32 lanes'
-//     taps: each lane writes its taps into its own column of a per-warp
-//     [16 bin x 32 lane] shared buffer at the rows of its bins, then each lane
-//     sums one bin-row half with vector loads; one shared atomic per
+//     taps: each lane writes its taps into its own (row-rotated) column of a
+//     per-warp [16 bin x 32 lane] shared buffer at the rows of its bins, then each
+//     lane sums one bin-row half with vector loads; one shared atomic per
 //     (bin, component) adds the warp's window to the CTA range tile, which is
 //     flushed to the IQ with one vector atomic per bin and channel.
+//  The adjoint runs the same per-pulse arithmetic and gathers the residual
+//  through the same taps instead of scattering.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -521,31 +524,30 @@ struct ScatterSink {
     float2 *tiles;  // [2][nc][WT]
     OutT *iq;
     int n, n0, np, buf;
-    __device__ __forceinline__ void operator()(const MixedArgs &A, int ch, const ChanRec &Q, int kb, const float h[8],
-                                               float vre, float vim, float, float, float, bool valid)
+    // two facets (packed path): one warp reduction each
+    __device__ __forceinline__ void put2(const MixedArgs &A, int ch, int kbase, int kba, int kbb, const float ha[8],
+                                         const float hb[8], float2 vre, float2 vim, float2, float2, float, bool va,
+                                         bool vb)
     {
         float2 *tile_c = tiles + (buf * A.S.nc + ch) * WT;
-        const int tile_base = Q.kbase - WT_LO;
+        const int tile_base = kbase - WT_LO;
         OutT *grow = iq + 2 * ((size_t)ch * np + (n - n0)) * A.S.nr;
-        warp_scatter<OutT>(stage, tile_c, tile_base, kb, valid, h, vre, vim, A.S.nr, grow, A.S.flags);
+        warp_scatter<OutT>(stage, tile_c, tile_base, kba, va, ha, vre.x, vim.x, A.S.nr, grow, A.S.flags);
+        warp_scatter<OutT>(stage, tile_c, tile_base, kbb, vb, hb, vre.y, vim.y, A.S.nr, grow, A.S.flags);
     }
 };
 
-// Adjoint sink: the transposed spread, a gather of the residual through the same
-// taps (g = sum_j h_j r[kb + j]), and the chain rule on the contribution s:
-// d/dsigma: Re(conj(g) s) / sigma;  d/d(u, v): 2 K0 t_n (r_t + r_r)_{x,y} Im(conj(g) s).
+// Adjoint sink of the packed path: the gathers of the two facets, then the
+// chain-rule terms accumulated as pairs.
 template <typename InT>
-struct GatherSink {
+struct GatherSink2 {
     const float2 *win;  // [nc][WT] residual window of the pulse
     const InT *resid;
     int n, n0, np;
-    float as, au, av;   // per-facet accumulators (sigma term, u and v terms without the factor 2)
-    __device__ __forceinline__ void operator()(const MixedArgs &A, int ch, const ChanRec &Q, int kb, const float h[8],
-                                               float vre, float vim, float qx, float qy, float k0t, bool)
+    float2 as, au, av;  // per-facet accumulators, facet a in .x, facet b in .y
+    __device__ __forceinline__ float2 gather(const MixedArgs &A, const float2 *wc, int tb, const InT *grow, int kb,
+                                             const float h[8]) const
     {
-        const float2 *wc = win + ch * WT;
-        const int tb = Q.kbase - WT_LO;
-        const InT *grow = resid + 2 * ((size_t)ch * np + (n - n0)) * A.S.nr;
         float gr = 0.0f, gi = 0.0f;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -561,107 +563,26 @@ struct GatherSink {
             gr = fmaf(h[j], v.x, gr);
             gi = fmaf(h[j], v.y, gi);
         }
-        const float re_gs = fmaf(gr, vre, gi * vim);
-        const float im_gs = fmaf(gr, vim, -gi * vre);
-        as += re_gs;
-        au = fmaf(-k0t * qx, im_gs, au);
-        av = fmaf(-k0t * qy, im_gs, av);
+        return make_float2(gr, gi);
+    }
+    __device__ __forceinline__ void put2(const MixedArgs &A, int ch, int kbase, int kba, int kbb, const float ha[8],
+                                         const float hb[8], float2 vre, float2 vim, float2 qx, float2 qy, float k0t,
+                                         bool, bool)
+    {
+        const float2 *wc = win + ch * WT;
+        const int tb = kbase - WT_LO;
+        const InT *grow = resid + 2 * ((size_t)ch * np + (n - n0)) * A.S.nr;
+        const float2 ga = gather(A, wc, tb, grow, kba, ha);
+        const float2 gb = gather(A, wc, tb, grow, kbb, hb);
+        const float2 GR = make_float2(ga.x, gb.x), GI = make_float2(ga.y, gb.y);
+        const float2 re_gs = fma2(GR, vre, mul2(GI, vim));
+        const float2 im_gs = fma2(GR, vim, neg2(mul2(GI, vre)));
+        as = add2(as, re_gs);
+        const float2 mk = dup(-k0t);
+        au = fma2(mul2(mk, qx), im_gs, au);
+        av = fma2(mul2(mk, qy), im_gs, av);
     }
 };
-
-template <int TAPS, typename Sink>
-__device__ __forceinline__ void facet_pulse(const Smem &sm, const MixedArgs &A, const PolyArgs &P,
-                                            const FacetGeo &G, const float c[3][kOrders], int pi, float xi_x,
-                                            float fi, Sink &sink)
-{
-    const DevScene &S = A.S;
-    const int nc = S.nc;
-    const PulseRec PR = sm.pr[pi];
-    const float eta = horner(c[0], PR.tau);
-    const float sx = horner(c[1], PR.tau);
-    const float sy = horner(c[2], PR.tau);
-    const float xi0 = xi_x, xi1 = G.xi_y, xi2 = eta;
-    const float b2 = fmaf(xi0, xi0, fmaf(xi1, xi1, eta * eta));
-    const float inv_n = rsqrtf(fmaf(sx, sx, fmaf(sy, sy, 1.0f)));
-
-    // transmit leg (shared by the channels)
-    const AntRec T = sm.tx[pi];
-    const float at = fmaf(T.ux, xi0, fmaf(T.uy, xi1, T.uz * xi2));
-    const float st = fmaf(-at, at, b2);
-    const float qt = st * fmaf(-at, T.inv2R2, T.inv2R);
-    const float dt = at + qt;
-    const float et = dt * T.invR;
-    const float rho_t = fmaf(et, et, 1.0f - et);
-    const float ut = (T.u0 + fmaf(xi0, T.aRx, fmaf(xi1, T.aRy, xi2 * T.aRz))) * rho_t;
-    const float vt = (T.v0 + fmaf(xi0, T.eRx, fmaf(xi1, T.eRy, xi2 * T.eRz))) * rho_t;
-    const float gt = sinc2f(P, A.tx_laz_l * ut) * sinc2f(P, A.tx_lel_l * vt);
-    const float rt0 = fmaf(xi0, T.invR, T.ux) * rho_t;
-    const float rt1 = fmaf(xi1, T.invR, T.uy) * rho_t;
-    const float rt2 = fmaf(xi2, T.invR, T.uz) * rho_t;
-    const float ampt = gt * T.ampr * rho_t;
-
-    const AntRec *RX = sm.rx + pi * nc;
-    const ChanRec *CH = sm.ch + pi * nc;
-    for (int ch = 0; ch < nc; ++ch) {
-        const AntRec R = RX[ch];
-        const ChanRec Q = CH[ch];
-        const float ar = fmaf(R.ux, xi0, fmaf(R.uy, xi1, R.uz * xi2));
-        const float sr_ = fmaf(-ar, ar, b2);
-        const float qr = sr_ * fmaf(-ar, R.inv2R2, R.inv2R);
-        const float dr = ar + qr;
-        const float er = dr * R.invR;
-        const float rho_r = fmaf(er, er, 1.0f - er);
-        const float ur = (R.u0 + fmaf(xi0, R.aRx, fmaf(xi1, R.aRy, xi2 * R.aRz))) * rho_r;
-        const float vr = (R.v0 + fmaf(xi0, R.eRx, fmaf(xi1, R.eRy, xi2 * R.eRz))) * rho_r;
-        const float gr = sinc2f(P, A.rx_laz_l[ch] * ur) * sinc2f(P, A.rx_lel_l[ch] * vr);
-        const float qx = -fmaf(fmaf(xi0, R.invR, R.ux), rho_r, rt0);
-        const float qy = -fmaf(fmaf(xi1, R.invR, R.uy), rho_r, rt1);
-        const float qz = -fmaf(fmaf(xi2, R.invR, R.uz), rho_r, rt2);
-        // sqrt(sigma0 A) with sigma0 = base (1 + m cos phi) max(0, n.Q) / (|n| Q_z):
-        // X = base A (1 + m cos phi) max(0, n.Q) / |n| = sigma0 A Q_z, so
-        // sqrt(sigma0 A) = X rsqrt(X Q_z) (one reciprocal square root)
-        float amp_s = G.amp_static;
-        if (!S.static_surface) {
-            float qh2 = fmaf(qx, qx, qy * qy);
-            float cphi = qh2 > 0.0f ? fmaf(A.wcos, qx, A.wsin * qy) * rsqrtf(qh2) : 0.0f;
-            float nq = fmaf(-sx, qx, fmaf(-sy, qy, qz));
-            float X = G.base_area * fmaf(A.wind_mod, cphi, 1.0f) * (fmaxf(nq, 0.0f) * inv_n);
-            amp_s = X > 0.0f ? X * rsqrtf(X * qz) : 0.0f;
-        }
-        const float amp = amp_s * ampt * gr * R.ampr * rho_r;
-        const float vc = -fmaf(G.cu, qx, G.cv * qy);
-        float phi = Q.psi + fmaf(fi, Q.ax, fmaf(G.fj, Q.ay, fmaf(Q.gam, eta, -A.k0 * (qt + qr))));
-        phi = fmaf(-PR.k0t, vc, phi);
-        phi = reduce_phase(phi);
-        float sp, cp;
-        __sincosf(phi, &sp, &cp);
-        const float zr = amp * G.z.x, zi = amp * G.z.y;
-        const float vre = zr * cp - zi * sp;
-        const float vim = fmaf(zr, sp, zi * cp);
-        const float p = fmaf(dt + dr, A.inv_dr, Q.pfrac);
-        const float kf = floorf(p);
-        const float fr = p - kf;
-        int kb;
-        float h[8];
-        if (TAPS == 1) {
-            kb = Q.kbase + (int)kf;
-            h[0] = 1.0f;
-#pragma unroll
-            for (int j = 1; j < 8; ++j) h[j] = 0.0f;
-        } else {
-            kb = Q.kbase + (int)kf - 3;
-            const float t = fmaf(2.0f, fr, -1.0f);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                float v = P.tap[j][kTapDeg].x;
-#pragma unroll
-                for (int d = kTapDeg - 1; d >= 0; --d) v = fmaf(v, t, P.tap[j][d].x);
-                h[j] = v;
-            }
-        }
-        sink(A, ch, Q, kb, h, vre, vim, qx, qy, PR.k0t, G.valid);
-    }
-}
 
 // Per-thread pair of facets (same column, rows w and w + 8) for the packed path.
 struct PairGeo {
@@ -680,10 +601,9 @@ __device__ __forceinline__ float2 horner2(const float2 c[kOrders], float2 t)
 // Forward contribution of the thread's two facets for pulse pi (chunk index),
 // every channel: the same arithmetic as facet_pulse, on FP32x2 pairs (facet a in
 // .x, facet b in .y); transcendentals and integer work per element.
-template <int TAPS, typename OutT>
+template <int TAPS, typename Sink>
 __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A, const PolyArgs &P, const PairGeo &G,
-                                             const float2 C[3][kOrders], int pi, float xi_x, float fi,
-                                             ScatterSink<OutT> &sink)
+                                             const float2 C[3][kOrders], int pi, float xi_x, float fi, Sink &sink)
 {
     const DevScene &S = A.S;
     const int nc = S.nc;
@@ -784,11 +704,7 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
                 hb[j] = v.y;
             }
         }
-        float2 *tile_c = sink.tiles + (sink.buf * nc + ch) * WT;
-        const int tile_base = Q.kbase - WT_LO;
-        OutT *grow = sink.iq + 2 * ((size_t)ch * sink.np + (sink.n - sink.n0)) * S.nr;
-        warp_scatter<OutT>(sink.stage, tile_c, tile_base, kba, G.va, ha, vre.x, vim.x, S.nr, grow, S.flags);
-        warp_scatter<OutT>(sink.stage, tile_c, tile_base, kbb, G.vb, hb, vre.y, vim.y, S.nr, grow, S.flags);
+        sink.put2(A, ch, Q.kbase, kba, kbb, ha, hb, vre, vim, qx, qy, PR.k0t, G.va, G.vb);
     }
 }
 
@@ -921,7 +837,7 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
             G.zi = make_float2(ga.z.y, two ? gb.z.y : 0.0f);
             sink.n = n;
             sink.buf = buf;
-            facet_pulse2<TAPS, OutT>(sm, A, P, G, C, pi, xi_x, fi, sink);
+            facet_pulse2<TAPS>(sm, A, P, G, C, pi, xi_x, fi, sink);
             __syncthreads();
             for (int i = threadIdx.x; i < nc * WT; i += NT) {
                 int ch = i / WT, w = i % WT;
@@ -1066,7 +982,7 @@ __global__ void __launch_bounds__(NT, 2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DevScene &S = A.S;
     const int nc = S.nc;
-    const Smem sm = carve(smem_raw, nc, false);
+    const Smem sm = carve(smem_raw, nc, true);
     const int tiles_x = (S.nx + TX - 1) / TX;
     const int tx0 = (blockIdx.x % tiles_x) * TX;
     const int ty0 = (blockIdx.x / tiles_x) * TY;
@@ -1094,23 +1010,37 @@ __global__ void __launch_bounds__(NT, 2)
 #pragma unroll
             for (int o = 0; o < kOrders; ++o) ca[f][o] = cb[f][o] = 0.0f;
     }
-    GatherSink<InT> ka, kb;
-    ka.win = kb.win = sm.tile;
-    ka.resid = kb.resid = resid;
-    ka.n0 = kb.n0 = n0;
-    ka.np = kb.np = np;
-    ka.as = ka.au = ka.av = kb.as = kb.au = kb.av = 0.0f;
+    PairGeo G;
+    G.xi_y = make_float2(ga.xi_y, gb.xi_y);
+    G.fj = make_float2(ga.fj, gb.fj);
+    G.base_area = make_float2(ga.base_area, gb.base_area);
+    G.amp_static = make_float2(ga.amp_static, gb.amp_static);
+    G.cu = make_float2(ga.cu, gb.cu);
+    G.cv = make_float2(ga.cv, gb.cv);
+    G.va = ga.valid;
+    G.vb = gb.valid;
+    float2 C[3][kOrders];
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int o = 0; o < kOrders; ++o) C[f][o] = make_float2(ca[f][o], cb[f][o]);
+    GatherSink2<InT> sink;
+    sink.win = sm.tile;
+    sink.resid = resid;
+    sink.n0 = n0;
+    sink.np = np;
+    sink.as = sink.au = sink.av = make_float2(0.0f, 0.0f);
     for (int n = pa; n < pe; ++n) {
         const int pi = (n - pa) % NBR;
         if (pi == 0) {
             __syncthreads();  // the previous chunk is done with the records
-            build_refs<false>(sm, A, n, min(n + NBR, pe), xr, yr);
+            build_refs<true>(sm, A, n, min(n + NBR, pe), xr, yr);
         }
         __syncthreads();
         // residual window of this pulse, every channel
         for (int i = threadIdx.x; i < nc * WT; i += NT) {
             int ch = i / WT, w = i % WT;
-            int k = sm.ch[pi * nc + ch].kbase - WT_LO + w;
+            int k = sm.ch2[pi * nc + ch].kbase - WT_LO + w;
             float2 v = make_float2(0.f, 0.f);
             if (k >= 0 && k < S.nr) {
                 const InT *r = resid + 2 * (((size_t)ch * np + (n - n0)) * S.nr + k);
@@ -1128,12 +1058,13 @@ __global__ void __launch_bounds__(NT, 2)
             gb.z = speckle_f(S.speckle_seed, gb.fid, (uint32_t)e);
             gb.epoch = e;
         }
-        ka.n = kb.n = n;
-        facet_pulse<TAPS>(sm, A, P, ga, ca, pi, xi_x, fi, ka);
-        facet_pulse<TAPS>(sm, A, P, gb, cb, pi, xi_x, fi, kb);
+        G.zr = make_float2(ga.z.x, gb.z.x);
+        G.zi = make_float2(ga.z.y, gb.z.y);
+        sink.n = n;
+        facet_pulse2<TAPS>(sm, A, P, G, C, pi, xi_x, fi, sink);
     }
-    add_cell_grads(ga, ka.as, ka.au, ka.av, g_sigma, g_uv);
-    add_cell_grads(gb, kb.as, kb.au, kb.av, g_sigma, g_uv);
+    add_cell_grads(ga, sink.as.x, sink.au.x, sink.av.x, g_sigma, g_uv);
+    add_cell_grads(gb, sink.as.y, sink.au.y, sink.av.y, g_sigma, g_uv);
 }
 
 // Facet generator of the mixed path: same Taylor expansion, states written out.
@@ -1282,7 +1213,7 @@ cudaError_t launch_adjoint_mixed(const DevScene &S, const MixedTables &M, cudaSt
 {
     MixedArgs A = make_args(S, M);
     PolyArgs P = make_poly(M);
-    const int bytes = layout(S.nc, false).total;
+    const int bytes = layout(S.nc, true).total;
     int tiles = ((S.nx + TX - 1) / TX) * ((S.ny + TY - 1) / TY);
     int b0 = n0 / M.nb, b1 = (n0 + np - 1) / M.nb;
     cudaError_t e;
