@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--pulses", type=int, default=2048, help="burst length of the scene")
     ap.add_argument("--window", type=int, default=0,
                     help="pulses per step (0 = the whole burst); for the slow FP64 form")
-    ap.add_argument("--cpu-pulses", type=int, default=1, help="pulses in the oracle sample")
+    ap.add_argument("--cpu-pulses", type=int, default=4,
+                    help="pulses in the oracle sample (4 pulses: ~10 s on 16 host cores)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-scene batched measurement")
@@ -116,13 +117,36 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# Work per contribution of the mixed accumulator (FP32 flops, FFMA = 2): the
-# formulation's arithmetic as counted by the instruction-mix counters on the
-# 512-pulse capture of the headline scene (150 FFMA + 52 FMUL + 42 FADD), with the
-# generator's time-Taylor contraction amortised over 128 pulses and 6 channels.
-FLOPS_PER_CONTRIBUTION = 394.0
+# Work per contribution of the mixed accumulator (FP32 flops: FFMA2 = 4, FFMA and
+# FMUL2/FADD2 = 2, FMUL/FADD = 1): the formulation's arithmetic as counted by the
+# instruction-mix counters on the 512-pulse capture of the headline scene (per
+# contribution 69.0 FFMA2 + 13.0 FFMA + 15.7 FMUL2 + 19.8 FMUL + 15.0 FADD2 + 3.3
+# FADD), with the generator's time-Taylor contraction amortised over 128 pulses and
+# 6 channels.
+FLOPS_PER_CONTRIBUTION = 386.6
 # All instructions issued per contribution (thread level, same capture).
-INSTR_PER_CONTRIBUTION = 462.0
+INSTR_PER_CONTRIBUTION = 355.9
+# DRAM bytes (read + write) of one headline launch (2048 pulses), from one ncu
+# capture of dram__bytes_read.sum + dram__bytes_write.sum, and the SHA-256 of the
+# kernel sources it was taken on: the figure is reported only while they match.
+TRAFFIC_BYTES = 81734400 + 29260032
+TRAFFIC_PULSES = 2048
+TRAFFIC_SOURCES = ("echo_mixed.cu", "harm_kernels.cuh", "harm_internal.cuh")
+TRAFFIC_SHA256 = "0c2cda365086c3921490c70fd1890b059fb46987f1b844bfe73de1592a3a6dbf"
+
+
+def captured_traffic(np_step):
+    """DRAM bytes per launch from the stored capture, or None when the launch
+    differs from the captured one or the kernel sources changed since."""
+    import hashlib
+    if np_step != TRAFFIC_PULSES:
+        return None
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2405_09938_b300", "csrc")
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return float(TRAFFIC_BYTES) if h.hexdigest() == TRAFFIC_SHA256 else None
 
 
 def max_over_ranks(total_ms, dist=None, device="cpu"):
@@ -299,7 +323,8 @@ def main():
                    "replicas": world},
         "roofline": {"bound": "alu", "achieved": achieved if prec == harm.HARM_PREC_MIXED else None,
                      "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak if prec == harm.HARM_PREC_MIXED else None, "traffic": None,
+                     "frac": achieved / fp32_peak if prec == harm.HARM_PREC_MIXED else None,
+                     "traffic": captured_traffic(np_step) if prec == harm.HARM_PREC_MIXED else None,
                      "kernel": "accumulate_mixed_kernel" if prec == harm.HARM_PREC_MIXED else "accumulate_f64_kernel",
                      "kernel_ms": kern_ms, "flops_per_contribution": flops / units,
                      "peak_basis": "148 SM x 128 FP32 lanes x 2 x %.0f MHz (max SM clock)" % sm_max,
