@@ -172,6 +172,86 @@ def batch_scenes(n_scenes=48, seed=11):
     return out
 
 
+# ---------------------------------------------------------------------------
+# Variants of the surface and scattering model (Sec. III): each takes a
+# descriptor and returns a copy with the variant switched on.
+# ---------------------------------------------------------------------------
+def ar1_speckle(desc, tau_s=0.05, doppler_hz=12.0, epoch_pulses=8):
+    """Order-1 autoregressive speckle (Eq. 10) with correlation time tau_s,
+    updated every epoch of ``epoch_pulses`` pulses, and a uniform intra-facet
+    Doppler shift f_s (Eq. 7)."""
+    d = copy.deepcopy(desc)
+    d.update({"speckle_tau_s": float(tau_s), "speckle_doppler_hz": float(doppler_hz),
+              "epoch_pulses": int(epoch_pulses)})
+    return d
+
+
+def choppy(desc):
+    """Choppy Wave Model on: facets follow the waves' orbital motion horizontally."""
+    d = copy.deepcopy(desc)
+    d["cwm"] = 1
+    return d
+
+
+def hetero_sea(desc, tile_m=512.0, u10=(6.0, 12.0), wind_dir_deg=(20.0, 80.0)):
+    """Heterogeneous sea state (Eq. 1, 2): TL tiles of ``tile_m`` from the patch
+    corner, with a corner grid just covering the patch. The corner spectra vary
+    smoothly: wind speed ramps linearly along x over ``u10``, wind direction
+    along y over ``wind_dir_deg``."""
+    d = copy.deepcopy(desc)
+    lx, ly = d["nx"] * d["facet_m"], d["ny"] * d["facet_m"]
+    ncx = int(math.ceil(lx / tile_m - 1e-9)) + 1
+    ncy = int(math.ceil(ly / tile_m - 1e-9)) + 1
+    ax = np.linspace(0.0, 1.0, ncx)
+    ay = np.linspace(0.0, 1.0, ncy)
+    u = u10[0] + (u10[1] - u10[0]) * np.tile(ax, (ncy, 1))
+    w = np.radians(wind_dir_deg[0] + (wind_dir_deg[1] - wind_dir_deg[0]) * np.tile(ay[:, None], (1, ncx)))
+    d["hetero"] = {"tile_m": float(tile_m), "u10": u, "wind_dir": w}
+    return d
+
+
+def phased_array_gain(len_az, len_el, seed, nu=161, nv=81, u_span=0.02, v_span=0.02,
+                      tiles=(14, 4), amp_err_db=0.5, phase_err_deg=5.0):
+    """Complex u-v gain grid of a planar phased array (the form in which the
+    antenna patterns reach the simulator, Sec. III-B): the aperture
+    len_az x len_el split into tiles[0] x tiles[1] sub-arrays, each with a
+    uniform field sinc(L_t u / lambda) sinc(H_t v / lambda) and a random complex
+    excitation error (amplitude ``amp_err_db`` rms in dB, phase
+    ``phase_err_deg`` rms) from numpy's Philox generator; normalised to unit
+    gain at boresight of the error-free array. Grid: nu x nv nodes over
+    [-u_span/2, u_span/2] x [-v_span/2, v_span/2] (direction cosines along the
+    azimuth and elevation axes). Returns the pattern dict of a descriptor."""
+    lam = C_LIGHT / F0_HZ
+    rng = np.random.Generator(np.random.Philox(seed))
+    mt, nt = tiles
+    lt, ht = len_az / mt, len_el / nt
+    xt = (np.arange(mt) + 0.5 - 0.5 * mt) * lt
+    zt = (np.arange(nt) + 0.5 - 0.5 * nt) * ht
+    err = (10.0 ** (amp_err_db / 20.0 * rng.standard_normal((nt, mt)))
+           * np.exp(1j * np.radians(phase_err_deg) * rng.standard_normal((nt, mt))))
+    u = np.linspace(-0.5 * u_span, 0.5 * u_span, nu)
+    v = np.linspace(-0.5 * v_span, 0.5 * v_span, nv)
+    k = 2.0 * math.pi / lam
+    ex = np.exp(1j * k * np.outer(u, xt))  # [nu, mt]
+    ez = np.exp(1j * k * np.outer(v, zt))  # [nv, nt]
+    af = np.einsum("vn,nm,um->vu", ez, err, ex)  # [nv, nu]
+    elem = np.outer(np.sinc(ht * v / lam), np.sinc(lt * u / lam))
+    g = af * elem / (mt * nt)
+    return {"u0": float(u[0]), "du": float(u[1] - u[0]), "v0": float(v[0]), "dv": float(v[1] - v[0]),
+            "gain": g}
+
+
+def uv_patterns(desc, seed=31):
+    """u-v gain grids for the transmitter and every receive channel (phase
+    centres of one satellite share their array but not its errors)."""
+    d = copy.deepcopy(desc)
+    pats = {"tx": phased_array_gain(d["tx"]["len_az"], d["tx"]["len_el"], seed)}
+    for c, a in enumerate(d["rx"]):
+        pats[c] = phased_array_gain(a["len_az"], a["len_el"], seed + 1 + c)
+    d["patterns"] = pats
+    return d
+
+
 def with_overrides(desc, **kw):
     d = copy.deepcopy(desc)
     d.update(kw)

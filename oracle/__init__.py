@@ -31,6 +31,11 @@ class _Antenna(C.Structure):
                 ("len_az", C.c_double), ("len_el", C.c_double)]
 
 
+class _Lut(C.Structure):
+    _fields_ = [("nu", C.c_int), ("nv", C.c_int), ("u0", C.c_double), ("du", C.c_double),
+                ("v0", C.c_double), ("dv", C.c_double), ("g", C.POINTER(C.c_double))]
+
+
 class OrScene(C.Structure):
     _fields_ = [
         ("f0", C.c_double), ("fs", C.c_double), ("prf", C.c_double),
@@ -54,6 +59,11 @@ class OrScene(C.Structure):
         ("ncx", C.c_int), ("ncy", C.c_int), ("cell", C.c_double),
         ("cell_sigma0", C.POINTER(C.c_double)),
         ("cell_uv", C.POINTER(C.c_double)),
+        ("tau_s", C.c_double), ("doppler_hz", C.c_double),
+        ("cwm", C.c_int),
+        ("het_l", C.c_double), ("het_ncx", C.c_int), ("het_ncy", C.c_int),
+        ("het_u10", C.POINTER(C.c_double)), ("het_dir", C.POINTER(C.c_double)),
+        ("lut", _Lut * (1 + MAXC)),
     ]
 
 
@@ -104,7 +114,19 @@ def lib():
         L.or_range_start.restype = C.c_double
         L.or_epoch.argtypes = [C.POINTER(OrScene), C.c_int]
         L.or_epoch.restype = C.c_uint32
-        L.or_facet_states.argtypes = [C.POINTER(OrScene), C.c_int, C.c_int, dp, dp, dp, dp, dp, dp]
+        L.or_facet_states.argtypes = [C.POINTER(OrScene), C.c_int, dp]
+        L.or_speckle_beta.argtypes = [C.POINTER(OrScene)]
+        L.or_speckle_beta.restype = C.c_double
+        L.or_speckle_ar1.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_double, dp, dp]
+        L.or_wave_table_corner.argtypes = [C.POINTER(OrScene), C.c_int, dp, dp, dp, dp, dp]
+        L.or_wave_table_corner.restype = C.c_int
+        L.or_surface_cwm.argtypes = [C.c_int, dp, dp, dp, dp, dp, C.c_double, C.c_double,
+                                     C.c_double, dp]
+        L.or_hetero_weight.argtypes = [C.POINTER(OrScene), C.c_int, C.c_int, C.c_double, C.c_double]
+        L.or_hetero_weight.restype = C.c_double
+        L.or_lut_gain.argtypes = [C.POINTER(_Lut), C.c_double, C.c_double, dp]
+        L.or_sigma0_normal.argtypes = [C.POINTER(OrScene), C.c_double, dp, dp, dp]
+        L.or_sigma0_normal.restype = C.c_double
         L.or_echo.argtypes = [C.POINTER(OrScene), C.c_int, C.POINTER(C.c_int), C.c_int64,
                               C.POINTER(C.c_int64), dp]
         L.or_echo.restype = C.c_int
@@ -157,11 +179,33 @@ class Scene:
                 a = np.ascontiguousarray(cells["uv"], dtype=np.float64)
                 self._keep.append(a)
                 s.cell_uv = _dptr(a)
+        s.tau_s = desc.get("speckle_tau_s", 0.0)
+        s.doppler_hz = desc.get("speckle_doppler_hz", 0.0)
+        s.cwm = int(desc.get("cwm", 0))
+        het = desc.get("hetero")
+        if het is not None:
+            u = np.ascontiguousarray(het["u10"], dtype=np.float64)
+            w = np.ascontiguousarray(het["wind_dir"], dtype=np.float64)
+            s.het_ncy, s.het_ncx = u.shape
+            s.het_l = het["tile_m"]
+            self._keep += [u, w]
+            s.het_u10, s.het_dir = _dptr(u), _dptr(w)
+        for ant, pat in (desc.get("patterns") or {}).items():
+            _fill_lut(s.lut[0 if ant == "tx" else 1 + int(ant)], pat, self._keep)
         self.s = s
 
     @property
     def ref(self):
         return C.byref(self.s)
+
+
+def _fill_lut(dst, pat, keep):
+    g = np.asarray(pat["gain"], dtype=np.complex128)
+    a = np.ascontiguousarray(np.stack([g.real, g.imag], axis=-1))
+    keep.append(a)
+    dst.nv, dst.nu = g.shape
+    dst.u0, dst.du, dst.v0, dst.dv = pat["u0"], pat["du"], pat["v0"], pat["dv"]
+    dst.g = _dptr(a)
 
 
 def _fill_antenna(dst, a):
@@ -255,21 +299,66 @@ def epoch(desc, n):
     return lib().or_epoch(Scene(desc).ref, n)
 
 
-def facet_states(desc, n):
-    """(eta, eta_x, eta_y) of every facet at pulse n: array [3, ny, nx]."""
+def facet_states(desc, n, fields=3):
+    """Facet states of every facet at pulse n: array [fields, ny, nx] of
+    (eta, eta_x, eta_y, D_x, D_y, dD_x/dx, dD_x/dy, dD_y/dy)[:fields]."""
     sc = Scene(desc)
-    nw = 0 if desc["static_surface"] else desc["n_omega"] * desc["n_theta"]
-    tab = wave_table(desc) if nw > 0 else {k: np.zeros(1) for k in ("kx", "ky", "omega", "amp",
-                                                                      "phase")}
-    out = np.zeros((3, desc["ny"], desc["nx"]))
-    lib().or_facet_states(sc.ref, n, nw, *[_dptr(tab[k]) for k in ("kx", "ky", "omega", "amp",
-                                                                    "phase")], _dptr(out))
+    out = np.zeros((8, desc["ny"], desc["nx"]))
+    lib().or_facet_states(sc.ref, n, _dptr(out))
+    return out[:fields].copy()
+
+
+def speckle_beta(desc):
+    return lib().or_speckle_beta(Scene(desc).ref)
+
+
+def speckle_ar1(seed, f, epoch, beta):
+    re, im = C.c_double(), C.c_double()
+    lib().or_speckle_ar1(seed, f, epoch, beta, C.byref(re), C.byref(im))
+    return complex(re.value, im.value)
+
+
+def wave_table_corner(desc, corner):
+    sc = Scene(desc)
+    n = desc["n_omega"] * desc["n_theta"]
+    arrs = [np.zeros(n) for _ in range(5)]
+    lib().or_wave_table_corner(sc.ref, corner, *[_dptr(a) for a in arrs])
+    return dict(zip(["kx", "ky", "omega", "amp", "phase"], arrs))
+
+
+def surface_cwm(table, x, y, t):
+    n = len(table["kx"])
+    out = np.zeros(8)
+    ts = [np.ascontiguousarray(table[k]) for k in ("kx", "ky", "omega", "amp", "phase")]
+    lib().or_surface_cwm(n, *[_dptr(a) for a in ts], float(x), float(y), float(t), _dptr(out))
     return out
 
 
-def contribution(desc, n, c, f, state):
+def hetero_weight(desc, cx, cy, x, y):
+    return lib().or_hetero_weight(Scene(desc).ref, cx, cy, float(x), float(y))
+
+
+def lut_gain(pat, u, v):
+    keep = []
+    L = _Lut()
+    _fill_lut(L, pat, keep)
+    out = np.zeros(2)
+    lib().or_lut_gain(C.byref(L), float(u), float(v), _dptr(out))
+    return complex(out[0], out[1])
+
+
+def sigma0_normal(desc, base, rt_hat, rr_hat, nvec):
     sc = Scene(desc)
-    st = np.ascontiguousarray(state, dtype=np.float64)
+    a, b, nv = [np.ascontiguousarray(v, dtype=np.float64) for v in (rt_hat, rr_hat, nvec)]
+    return lib().or_sigma0_normal(sc.ref, base, _dptr(a), _dptr(b), _dptr(nv))
+
+
+def contribution(desc, n, c, f, state):
+    """One facet's contribution and bin position; state holds (eta, eta_x,
+    eta_y) or all 8 fields of the facet state (missing fields are zero)."""
+    sc = Scene(desc)
+    st = np.zeros(8)
+    st[:len(state)] = state
     out = np.zeros(3)
     lib().or_contribution(sc.ref, n, c, f, _dptr(st), _dptr(out))
     return complex(out[0], out[1]), out[2]

@@ -21,6 +21,12 @@
  *   - The range-slice sum (Eq. 17) in its box form (taps = 1) and its
  *     Kaiser-windowed sinc form (taps = 2m), accumulated per bin with a
  *     Neumaier compensated sum (Neumaier 1974).
+ *   - Surface and scattering variants of Sec. III: the Choppy Wave Model
+ *     (horizontal displacement of the grid points along the waves' orbits),
+ *     heterogeneous sea states built from four overlapping homogeneous tiles
+ *     (Eq. 1, Eq. 2), the order-1 autoregressive speckle (Eq. 10) with the
+ *     intra-facet Doppler shift of Eq. 7, and antenna gains looked up in u-v
+ *     grids (Sec. III-B).
  *
  * Parity unpinned against the paper: the JONSWAP/spreading wave table and the
  * closed-form NRCS are not given by the paper; they are pinned only against
@@ -46,6 +52,15 @@ typedef struct {
     double len_az, len_el;
 } or_antenna;
 
+/* Complex antenna gain on a regular u-v grid (direction cosines along the
+   antenna's azimuth and elevation axes); g == NULL selects the analytic
+   sinc^2 pattern. */
+typedef struct {
+    int nu, nv;
+    double u0, du, v0, dv;
+    const double *g; /* [nv][nu][2] */
+} or_lut;
+
 typedef struct {
     double f0, fs, prf;
     int n_pulses, n_range;
@@ -70,6 +85,15 @@ typedef struct {
     double cell;
     const double *cell_sigma0; /* [ncy][ncx] */
     const double *cell_uv;     /* [ncy][ncx][2] */
+    /* variants of Sec. III (all off when zero / NULL) */
+    double tau_s;      /* AR(1) speckle correlation time (Eq. 10); 0 = independent epochs */
+    double doppler_hz; /* intra-facet Doppler shift f_s (Eq. 7) */
+    int cwm;           /* Choppy Wave Model horizontal displacement */
+    double het_l;      /* heterogeneous sea state: TL tile size L (Eq. 1, 2) */
+    int het_ncx, het_ncy;       /* corner grid, corner (cx, cy) at the patch corner + (cx, cy) L */
+    const double *het_u10;      /* [het_ncy][het_ncx] wind speed of corner spectrum S_i */
+    const double *het_dir;      /* [het_ncy][het_ncx] wind direction of corner spectrum S_i */
+    or_lut lut[1 + OR_MAXC];    /* [0] transmitter, [1 + c] receive channel c */
 } or_scene;
 
 /* ------------------------------------------------------------------------ */
@@ -125,6 +149,39 @@ void or_speckle(uint64_t seed, uint64_t f, uint32_t epoch, double *re, double *i
     *im = rad * sin(2.0 * OR_PI * u2);
 }
 
+/* AR(1) memory of the speckle between consecutive epochs (Eq. 10): beta =
+   exp(-T_e / tau_s) for the epoch duration T_e; tau_s = 0 gives beta = 0
+   (independent epochs). */
+double or_speckle_beta(const or_scene *s)
+{
+    if (!(s->tau_s > 0.0) || s->epoch_pulses <= 0) return 0.0;
+    return exp(-((double)s->epoch_pulses / s->prf) / s->tau_s);
+}
+
+/* Speckle of facet f in epoch e under the order-1 autoregressive model of
+   Eq. 10, applied to R and I alike: s_0 = w_0 and s_e = beta s_(e-1) +
+   sqrt(1 - beta^2) w_e, where w_e is the independent draw of or_speckle for
+   epoch e (R', I' of variance 1/2, so E|s_e|^2 = 1 for every e). The
+   recurrence is run from epoch 0. */
+void or_speckle_ar1(uint64_t seed, uint64_t f, uint32_t epoch, double beta, double *re, double *im)
+{
+    if (beta == 0.0) {
+        or_speckle(seed, f, epoch, re, im);
+        return;
+    }
+    double zr, zi;
+    or_speckle(seed, f, 0u, &zr, &zi);
+    double q = sqrt(1.0 - beta * beta);
+    for (uint32_t e = 1; e <= epoch; ++e) {
+        double wr, wi;
+        or_speckle(seed, f, e, &wr, &wi);
+        zr = beta * zr + q * wr;
+        zi = beta * zi + q * wi;
+    }
+    *re = zr;
+    *im = zi;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Sea state: JONSWAP spectrum, cos^2s spreading, 2-D linear wave grid.      */
 /* ------------------------------------------------------------------------ */
@@ -159,12 +216,13 @@ double or_spreading(double dtheta, double s)
    (geometric bin centres), n_theta directions centred on the wind, deep-water
    dispersion k = omega^2 / g, amplitude a = sqrt(2 S dω D dθ) and a uniform
    random phase drawn by Philox (wave stream) per component. */
-int or_wave_table(const or_scene *s, double *kx, double *ky, double *om, double *amp, double *ph)
+static int wave_table_for(const or_scene *s, double u10, double wind_dir, uint32_t word2, double *kx,
+                          double *ky, double *om, double *amp, double *ph)
 {
     int no = s->n_omega, nt = s->n_theta;
     if (no <= 0 || nt <= 0) return 0;
     double wp, alpha;
-    or_jonswap_params(s->u10, s->fetch, &wp, &alpha);
+    or_jonswap_params(u10, s->fetch, &wp, &alpha);
     double lo = 0.7 * wp, hi = 2.5 * wp;
     double dth = 2.0 * OR_PI / nt;
     for (int i = 0; i < no; ++i) {
@@ -172,22 +230,38 @@ int or_wave_table(const or_scene *s, double *kx, double *ky, double *om, double 
         double e1 = lo * pow(hi / lo, (double)(i + 1) / no);
         double w = sqrt(e0 * e1);
         double dw = e1 - e0;
-        double sw = or_jonswap(w, s->u10, s->fetch, s->gamma);
+        double sw = or_jonswap(w, u10, s->fetch, s->gamma);
         double k = w * w / OR_G;
         for (int j = 0; j < nt; ++j) {
             int m = i * nt + j;
-            double th = s->wind_dir - OR_PI + (j + 0.5) * dth;
-            double d = or_spreading(th - s->wind_dir, s->spread_s);
+            double th = wind_dir - OR_PI + (j + 0.5) * dth;
+            double d = or_spreading(th - wind_dir, s->spread_s);
             kx[m] = k * cos(th);
             ky[m] = k * sin(th);
             om[m] = w;
             amp[m] = sqrt(2.0 * sw * dw * d * dth);
             uint32_t r[4];
-            philox_draw(s->wave_seed, (uint32_t)m, 0u, OR_STREAM_WAVE, r);
+            philox_draw(s->wave_seed, (uint32_t)m, word2, OR_STREAM_WAVE, r);
             ph[m] = 2.0 * OR_PI * ((double)r[0] * (1.0 / 4294967296.0));
         }
     }
     return no * nt;
+}
+
+int or_wave_table(const or_scene *s, double *kx, double *ky, double *om, double *amp, double *ph)
+{
+    return wave_table_for(s, s->u10, s->wind_dir, 0u, kx, ky, om, amp, ph);
+}
+
+/* Wave table of the homogeneous tile T2L_i centred on corner i = cy * ncx + cx
+   of a heterogeneous sea state (Eq. 1): the corner's own spectrum S_i (wind
+   speed and direction; fetch, peak enhancement and spreading of the scene) and
+   its own random phases (Philox word 2 = 1 + i), uncorrelated with every other
+   corner. */
+int or_wave_table_corner(const or_scene *s, int corner, double *kx, double *ky, double *om, double *amp,
+                         double *ph)
+{
+    return wave_table_for(s, s->het_u10[corner], s->het_dir[corner], 1u + (uint32_t)corner, kx, ky, om, amp, ph);
 }
 
 /* Surface height and slopes at rest position (x, y), time t, by direct summation
@@ -206,6 +280,124 @@ void or_surface(int nw, const double *kx, const double *ky, const double *om, co
     out[0] = eta;
     out[1] = ex;
     out[2] = ey;
+}
+
+/* Choppy Wave Model (Sec. III; Nouguier, Guerin & Chapron, JGR 2009): the
+   grid point at rest position (x, y) moves horizontally by
+   D = -sum_j a_j (k_j / |k_j|) sin(theta_j) while its height is the linear
+   eta = sum_j a_j cos(theta_j), theta_j = k_j . (x, y) - omega_j t + phi_j.
+   out = (eta, deta/dx, deta/dy, D_x, D_y, dD_x/dx, dD_x/dy, dD_y/dy), every
+   derivative taken with respect to the rest position (dD_y/dx = dD_x/dy). */
+void or_surface_cwm(int nw, const double *kx, const double *ky, const double *om, const double *amp,
+                    const double *ph, double x, double y, double t, double out[8])
+{
+    for (int q = 0; q < 8; ++q) out[q] = 0.0;
+    for (int m = 0; m < nw; ++m) {
+        double arg = kx[m] * x + ky[m] * y - om[m] * t + ph[m];
+        double c = cos(arg), sn = sin(arg);
+        double k = sqrt(kx[m] * kx[m] + ky[m] * ky[m]);
+        double ux = kx[m] / k, uy = ky[m] / k;
+        out[0] += amp[m] * c;
+        out[1] -= amp[m] * kx[m] * sn;
+        out[2] -= amp[m] * ky[m] * sn;
+        out[3] -= amp[m] * ux * sn;
+        out[4] -= amp[m] * uy * sn;
+        out[5] -= amp[m] * ux * kx[m] * c;
+        out[6] -= amp[m] * ux * ky[m] * c;
+        out[7] -= amp[m] * uy * ky[m] * c;
+    }
+}
+
+/* The wave sets of a scene: one table for a homogeneous sea state, one per
+   corner of the TL-tile grid for a heterogeneous one. */
+typedef struct {
+    int n_sets, nw;
+    double *kx, *ky, *om, *amp, *ph; /* [n_sets][nw] */
+} or_waves;
+
+static void waves_build(const or_scene *s, or_waves *W)
+{
+    W->nw = s->static_surface ? 0 : s->n_omega * s->n_theta;
+    W->n_sets = s->het_ncx > 0 ? s->het_ncx * s->het_ncy : 1;
+    size_t n = (size_t)W->n_sets * (W->nw > 0 ? W->nw : 1);
+    W->kx = calloc(n, sizeof(double));
+    W->ky = calloc(n, sizeof(double));
+    W->om = calloc(n, sizeof(double));
+    W->amp = calloc(n, sizeof(double));
+    W->ph = calloc(n, sizeof(double));
+    if (W->nw == 0) return;
+    for (int i = 0; i < W->n_sets; ++i) {
+        size_t o = (size_t)i * W->nw;
+        if (s->het_ncx > 0)
+            or_wave_table_corner(s, i, W->kx + o, W->ky + o, W->om + o, W->amp + o, W->ph + o);
+        else
+            or_wave_table(s, W->kx + o, W->ky + o, W->om + o, W->amp + o, W->ph + o);
+    }
+}
+
+static void waves_free(or_waves *W)
+{
+    free(W->kx); free(W->ky); free(W->om); free(W->amp); free(W->ph);
+}
+
+/* TL tile of a rest position: the corner grid starts at the patch corner with
+   step L; positions on the last corner line belong to the tile before it. */
+static void hetero_tile(const or_scene *s, double x, double y, int *tx, int *ty)
+{
+    double lx = s->nx * s->facet, ly = s->ny * s->facet;
+    int ix = (int)floor((x + 0.5 * lx) / s->het_l);
+    int iy = (int)floor((y + 0.5 * ly) / s->het_l);
+    if (ix < 0) ix = 0;
+    if (ix > s->het_ncx - 2) ix = s->het_ncx - 2;
+    if (iy < 0) iy = 0;
+    if (iy > s->het_ncy - 2) iy = s->het_ncy - 2;
+    *tx = ix;
+    *ty = iy;
+}
+
+/* Weight W^i of corner i = (cx, cy) at rest position (x, y) (Eq. 2):
+   sqrt(1 - w_x - w_y + w_x w_y) with w_x = |x_i - x| / L, w_y = |y_i - y| / L,
+   for the four corners of the position's TL tile; zero for every other corner. */
+double or_hetero_weight(const or_scene *s, int cx, int cy, double x, double y)
+{
+    int tx, ty;
+    hetero_tile(s, x, y, &tx, &ty);
+    if (cx < tx || cx > tx + 1 || cy < ty || cy > ty + 1) return 0.0;
+    double xc = -0.5 * s->nx * s->facet + cx * s->het_l;
+    double yc = -0.5 * s->ny * s->facet + cy * s->het_l;
+    double wx = fabs(xc - x) / s->het_l, wy = fabs(yc - y) / s->het_l;
+    double v = 1.0 - wx - wy + wx * wy;
+    return v > 0.0 ? sqrt(v) : 0.0;
+}
+
+/* State of the facet at rest position (x, y) at scene time t: the 8 fields of
+   or_surface_cwm. A heterogeneous sea state sums the four overlapping
+   homogeneous tiles with the weights of Eq. 2 (Eq. 1), applied alike to every
+   field (the weights are constants of the position, so the slopes and the
+   displacement gradient are combined with the same weights). Without the CWM
+   the horizontal displacement and its gradient are zero (linear surface). */
+void or_facet_state(const or_scene *s, const or_waves *W, double x, double y, double t, double out[8])
+{
+    for (int q = 0; q < 8; ++q) out[q] = 0.0;
+    if (W->nw == 0) return;
+    if (s->het_ncx > 0) {
+        int tx, ty;
+        hetero_tile(s, x, y, &tx, &ty);
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                int cx = tx + dx, cy = ty + dy;
+                double w = or_hetero_weight(s, cx, cy, x, y);
+                if (w == 0.0) continue;
+                size_t o = (size_t)(cy * s->het_ncx + cx) * W->nw;
+                double tmp[8];
+                or_surface_cwm(W->nw, W->kx + o, W->ky + o, W->om + o, W->amp + o, W->ph + o, x, y, t, tmp);
+                for (int q = 0; q < 8; ++q) out[q] += w * tmp[q];
+            }
+    } else {
+        or_surface_cwm(W->nw, W->kx, W->ky, W->om, W->amp, W->ph, x, y, t, out);
+    }
+    if (!s->cwm)
+        for (int q = 3; q < 8; ++q) out[q] = 0.0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -301,6 +493,42 @@ double or_pattern(double len_az, double len_el, double lambda, const double d[3]
     return sa * sa * se * se;
 }
 
+/* Complex gain at direction cosines (u, v) from a u-v grid (Sec. III-B: the
+   patterns are converted to u-v grids and looked up per facet and pulse):
+   bilinear interpolation between the four surrounding nodes; zero outside the
+   grid. out = (re, im). */
+void or_lut_gain(const or_lut *L, double u, double v, double out[2])
+{
+    out[0] = out[1] = 0.0;
+    double fu = (u - L->u0) / L->du, fv = (v - L->v0) / L->dv;
+    if (!(fu >= 0.0 && fu <= (double)(L->nu - 1) && fv >= 0.0 && fv <= (double)(L->nv - 1))) return;
+    int iu = (int)floor(fu), iv = (int)floor(fv);
+    if (iu > L->nu - 2) iu = L->nu - 2;
+    if (iv > L->nv - 2) iv = L->nv - 2;
+    double a = fu - iu, b = fv - iv;
+    const double *g00 = L->g + 2 * ((size_t)iv * L->nu + iu);
+    const double *g10 = g00 + 2;
+    const double *g01 = g00 + 2 * (size_t)L->nu;
+    const double *g11 = g01 + 2;
+    for (int q = 0; q < 2; ++q)
+        out[q] = (1.0 - a) * (1.0 - b) * g00[q] + a * (1.0 - b) * g10[q] + (1.0 - a) * b * g01[q] + a * b * g11[q];
+}
+
+/* Gain of one antenna for the unit direction d from its phase centre: the u-v
+   grid when one is set, else the analytic sinc^2 pattern (real). */
+static void antenna_gain(const or_lut *L, double len_az, double len_el, double lambda, const double d[3],
+                         const double a[3], const double e[3], double out[2])
+{
+    if (L->g) {
+        double u = d[0] * a[0] + d[1] * a[1] + d[2] * a[2];
+        double v = d[0] * e[0] + d[1] * e[1] + d[2] * e[2];
+        or_lut_gain(L, u, v, out);
+    } else {
+        out[0] = or_pattern(len_az, len_el, lambda, d, a, e);
+        out[1] = 0.0;
+    }
+}
+
 /* Modified Bessel function I0 by its power series sum_k ((x/2)^k / k!)^2. */
 double or_bessel_i0(double x)
 {
@@ -326,18 +554,26 @@ double or_kaiser_sinc(double x, int m, double beta)
    facet) and k_s = -r_r (facet to Rx); the wind term uses the angle between the
    wind direction and the horizontal part of Q (the bistatic angle of Eq. 12);
    the tilt factor is max(0, n.Q) / (|n| Q_z) for the facet normal n. */
-double or_sigma0(const or_scene *s, double base, const double rt_hat[3], const double rr_hat[3],
-                 double slope_x, double slope_y)
+double or_sigma0_normal(const or_scene *s, double base, const double rt_hat[3], const double rr_hat[3],
+                        const double nvec[3])
 {
     if (s->static_surface) return base;
     double q[3] = {-(rt_hat[0] + rr_hat[0]), -(rt_hat[1] + rr_hat[1]), -(rt_hat[2] + rr_hat[2])};
     double qh = sqrt(q[0] * q[0] + q[1] * q[1]);
     double cphi = 0.0;
     if (qh > 0.0) cphi = (cos(s->wind_dir) * q[0] + sin(s->wind_dir) * q[1]) / qh;
-    double nvec[3] = {-slope_x, -slope_y, 1.0};
     double ndotq = nvec[0] * q[0] + nvec[1] * q[1] + nvec[2] * q[2];
     double tilt = (ndotq > 0.0 ? ndotq : 0.0) / (norm3(nvec) * q[2]);
     return base * (1.0 + s->wind_mod * cphi) * tilt;
+}
+
+/* The same for a facet of the linear surface with slopes (slope_x, slope_y):
+   normal n = (-slope_x, -slope_y, 1). */
+double or_sigma0(const or_scene *s, double base, const double rt_hat[3], const double rr_hat[3],
+                 double slope_x, double slope_y)
+{
+    double nvec[3] = {-slope_x, -slope_y, 1.0};
+    return or_sigma0_normal(s, base, rt_hat, rr_hat, nvec);
 }
 
 static int cell_index(const or_scene *s, double x, double y)
@@ -361,10 +597,16 @@ double or_range_start(const or_scene *s, int c)
     return g.rt_ref + g.rr_ref - 0.5 * s->n_range * (OR_C / s->fs);
 }
 
-/* One facet's complex contribution at pulse state g (Eq. 3, 4, 16) and its
-   fractional range-bin position p. state = (eta, eta_x, eta_y). */
+/* One facet's complex contribution at pulse state g (Eq. 3, 4, 7, 16) and its
+   fractional range-bin position p. state = the 8 fields of or_facet_state. The
+   facet sits at its rest position moved by the horizontal displacement (zero
+   without the CWM) and lifted to eta; its normal is the cross product of the
+   tangents (1 + dD_x/dx, dD_x/dy, deta/dx) and (dD_x/dy, 1 + dD_y/dy, deta/dy)
+   of the displaced surface, and its area is the facet area times the normal's
+   vertical component (the horizontal area of the displaced facet; 1 for the
+   linear surface). */
 static void contribution_full(const or_scene *s, const or_pulse *g, int n, int c, int64_t f,
-                              const double state[3], double r0, double *sre, double *sim, double *p,
+                              const double state[8], double r0, double *sre, double *sim, double *p,
                               double *sumx, double *sumy, int *cell)
 {
     double lambda = OR_C / s->f0;
@@ -372,14 +614,15 @@ static void contribution_full(const or_scene *s, const or_pulse *g, int n, int c
     int ix = (int)(f % s->nx), iy = (int)(f / s->nx);
     double x = (ix + 0.5 - 0.5 * s->nx) * s->facet;
     double y = (iy + 0.5 - 0.5 * s->ny) * s->facet;
-    double xf[3] = {x, y, state[0]};
+    double xf[3] = {x + state[3], y + state[4], state[0]};
     double dt[3] = {xf[0] - g->ptx[0], xf[1] - g->ptx[1], xf[2] - g->ptx[2]};
     double dr[3] = {xf[0] - g->prx[0], xf[1] - g->prx[1], xf[2] - g->prx[2]};
     double rt = norm3(dt), rr = norm3(dr);
     double ut[3] = {dt[0] / rt, dt[1] / rt, dt[2] / rt};
     double ur[3] = {dr[0] / rr, dr[1] / rr, dr[2] / rr};
-    double gt = or_pattern(s->tx.len_az, s->tx.len_el, lambda, ut, g->atx, g->etx);
-    double gr = or_pattern(s->rx[c].len_az, s->rx[c].len_el, lambda, ur, g->arx, g->erx);
+    double gt[2], gr[2];
+    antenna_gain(&s->lut[0], s->tx.len_az, s->tx.len_el, lambda, ut, g->atx, g->etx, gt);
+    antenna_gain(&s->lut[1 + c], s->rx[c].len_az, s->rx[c].len_el, lambda, ur, g->arx, g->erx, gr);
     double base = s->sigma0_base, cu = s->cur_u, cv = s->cur_v;
     if (s->cell_sigma0 || s->cell_uv) {
         int ci = cell_index(s, x, y);
@@ -389,26 +632,33 @@ static void contribution_full(const or_scene *s, const or_pulse *g, int n, int c
             cv = s->cell_uv[2 * ci + 1];
         }
     }
-    double sig = or_sigma0(s, base, ut, ur, state[1], state[2]);
-    double area = s->facet * s->facet;
-    double amp = sqrt(sig * area) * gt * gr * (g->rt_ref * g->rr_ref) / (rt * rr);
+    double tx_[3] = {1.0 + state[5], state[6], state[1]};
+    double ty_[3] = {state[6], 1.0 + state[7], state[2]};
+    double nvec[3] = {tx_[1] * ty_[2] - tx_[2] * ty_[1], tx_[2] * ty_[0] - tx_[0] * ty_[2],
+                      tx_[0] * ty_[1] - tx_[1] * ty_[0]};
+    double sig = or_sigma0_normal(s, base, ut, ur, nvec);
+    double area = s->facet * s->facet * (nvec[2] > 0.0 ? nvec[2] : 0.0);
+    double amp = sqrt(sig * area) * (g->rt_ref * g->rr_ref) / (rt * rr);
     uint32_t e = s->epoch_pulses > 0 ? (uint32_t)(n / s->epoch_pulses) : 0u;
     double zr, zi;
-    or_speckle(s->speckle_seed, (uint64_t)f, e, &zr, &zi);
+    or_speckle_ar1(s->speckle_seed, (uint64_t)f, e, or_speckle_beta(s), &zr, &zi);
     double vc = cu * (ut[0] + ur[0]) + cv * (ut[1] + ur[1]);
-    double phase = -k0 * (rt + rr + vc * g->t);
+    double phase = -k0 * (rt + rr + vc * g->t) + 2.0 * OR_PI * s->doppler_hz * g->t;
     if (sumx) *sumx = ut[0] + ur[0];
     if (sumy) *sumy = ut[1] + ur[1];
     if (cell) *cell = (s->ncx > 0) ? cell_index(s, x, y) : -1;
+    /* field weight G_t G_r (complex for u-v grids) times the speckle */
+    double gre = gt[0] * gr[0] - gt[1] * gr[1], gim = gt[0] * gr[1] + gt[1] * gr[0];
+    double wr = zr * gre - zi * gim, wi = zr * gim + zi * gre;
     double cph = cos(phase), sph = sin(phase);
-    double ar = amp * zr, ai = amp * zi;
+    double ar = amp * wr, ai = amp * wi;
     *sre = ar * cph - ai * sph;
     *sim = ar * sph + ai * cph;
     *p = (rt + rr - r0) / (OR_C / s->fs);
 }
 
 static void contribution(const or_scene *s, const or_pulse *g, int n, int c, int64_t f,
-                         const double state[3], double r0, double *sre, double *sim, double *p)
+                         const double state[8], double r0, double *sre, double *sim, double *p)
 {
     contribution_full(s, g, n, c, f, state, r0, sre, sim, p, NULL, NULL, NULL);
 }
@@ -456,50 +706,48 @@ uint32_t or_epoch(const or_scene *s, int n)
     return s->epoch_pulses > 0 ? (uint32_t)(n / s->epoch_pulses) : 0u;
 }
 
-/* Facet states (eta, eta_x, eta_y) of all facets at pulse n (scene time t_s at
-   the scene centre), written to out[3][nf]. Zero for a static surface. */
-void or_facet_states(const or_scene *s, int n, int nw, const double *kx, const double *ky,
-                     const double *om, const double *amp, const double *ph, double *out)
+/* Facet states (the 8 fields of or_facet_state) of all facets at pulse n, at
+   the scene time t_s of the scene centre, written to out[8][nf]. Zero for a
+   static surface. */
+static void facet_states_w(const or_scene *s, const or_waves *W, int n, double *out)
 {
     int64_t nf = (int64_t)s->nx * s->ny;
     or_pulse g;
     or_pulse_state(s, n, 0, &g);
-    if (s->static_surface || nw == 0) {
-        memset(out, 0, sizeof(double) * 3 * nf);
-        return;
-    }
 #pragma omp parallel for schedule(static)
     for (int64_t f = 0; f < nf; ++f) {
         int ix = (int)(f % s->nx), iy = (int)(f / s->nx);
         double x = (ix + 0.5 - 0.5 * s->nx) * s->facet;
         double y = (iy + 0.5 - 0.5 * s->ny) * s->facet;
-        double st[3];
-        or_surface(nw, kx, ky, om, amp, ph, x, y, g.ts, st);
-        out[f] = st[0];
-        out[nf + f] = st[1];
-        out[2 * nf + f] = st[2];
+        double st[8];
+        or_facet_state(s, W, x, y, g.ts, st);
+        for (int q = 0; q < 8; ++q) out[q * nf + f] = st[q];
     }
 }
 
-/* Facet states of the listed facets at pulse n: out[3][count] in list order. */
-static void list_states(const or_scene *s, int n, int nw, const double *kx, const double *ky, const double *om,
-                        const double *amp, const double *ph, int64_t count, const int64_t *facets, double *out)
+void or_facet_states(const or_scene *s, int n, double *out)
+{
+    or_waves W;
+    waves_build(s, &W);
+    facet_states_w(s, &W, n, out);
+    waves_free(&W);
+}
+
+/* Facet states of the listed facets at pulse n: out[8][count] in list order. */
+static void list_states(const or_scene *s, const or_waves *W, int n, int64_t count, const int64_t *facets,
+                        double *out)
 {
     or_pulse g;
     or_pulse_state(s, n, 0, &g);
 #pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < count; ++q) {
-        double st[3] = {0.0, 0.0, 0.0};
-        if (!s->static_surface && nw > 0) {
-            int64_t f = facets[q];
-            int ix = (int)(f % s->nx), iy = (int)(f / s->nx);
-            double x = (ix + 0.5 - 0.5 * s->nx) * s->facet;
-            double y = (iy + 0.5 - 0.5 * s->ny) * s->facet;
-            or_surface(nw, kx, ky, om, amp, ph, x, y, g.ts, st);
-        }
-        out[q] = st[0];
-        out[count + q] = st[1];
-        out[2 * count + q] = st[2];
+        int64_t f = facets[q];
+        int ix = (int)(f % s->nx), iy = (int)(f / s->nx);
+        double x = (ix + 0.5 - 0.5 * s->nx) * s->facet;
+        double y = (iy + 0.5 - 0.5 * s->ny) * s->facet;
+        double st[8];
+        or_facet_state(s, W, x, y, g.ts, st);
+        for (int k = 0; k < 8; ++k) out[k * count + q] = st[k];
     }
 }
 
@@ -511,25 +759,19 @@ int or_echo(const or_scene *s, int n_list, const int *pulses, int64_t n_fac, con
 {
     int nc = s->n_channels, nr = s->n_range;
     int64_t nf = (int64_t)s->nx * s->ny;
-    int nw = (s->static_surface ? 0 : s->n_omega * s->n_theta);
-    double *kx = NULL, *ky = NULL, *om = NULL, *amp = NULL, *ph = NULL;
-    if (nw > 0) {
-        kx = malloc(sizeof(double) * nw); ky = malloc(sizeof(double) * nw);
-        om = malloc(sizeof(double) * nw); amp = malloc(sizeof(double) * nw);
-        ph = malloc(sizeof(double) * nw);
-        or_wave_table(s, kx, ky, om, amp, ph);
-    }
+    or_waves W;
+    waves_build(s, &W);
     int64_t nsum = facets ? n_fac : nf;
-    /* states of the summed facets only: st[3][nsum] in list order */
-    double *st = malloc(sizeof(double) * 3 * (nsum > 0 ? nsum : 1));
+    /* states of the summed facets only: st[8][nsum] in list order */
+    double *st = malloc(sizeof(double) * 8 * (nsum > 0 ? nsum : 1));
     double r0[OR_MAXC];
     for (int c = 0; c < nc; ++c) r0[c] = or_range_start(s, c);
     for (int i = 0; i < n_list; ++i) {
         int n = pulses[i];
         if (facets)
-            list_states(s, n, nw, kx, ky, om, amp, ph, nsum, facets, st);
+            list_states(s, &W, n, nsum, facets, st);
         else
-            or_facet_states(s, n, nw, kx, ky, om, amp, ph, st);
+            facet_states_w(s, &W, n, st);
 #pragma omp parallel for schedule(dynamic, 1)
         for (int c = 0; c < nc; ++c) {
             or_pulse g;
@@ -538,7 +780,8 @@ int or_echo(const or_scene *s, int n_list, const int *pulses, int64_t n_fac, con
             double *si = calloc(nr, sizeof(double)), *ci = calloc(nr, sizeof(double));
             for (int64_t q = 0; q < nsum; ++q) {
                 int64_t f = facets ? facets[q] : q;
-                double state[3] = {st[q], st[nsum + q], st[2 * nsum + q]};
+                double state[8];
+                for (int k = 0; k < 8; ++k) state[k] = st[k * nsum + q];
                 double sre, sim, p;
                 contribution(s, &g, n, c, f, state, r0[c], &sre, &sim, &p);
                 spread(s, sre, sim, p, sr, cr, si, ci);
@@ -552,13 +795,13 @@ int or_echo(const or_scene *s, int n_list, const int *pulses, int64_t n_fac, con
         }
     }
     free(st);
-    free(kx); free(ky); free(om); free(amp); free(ph);
+    waves_free(&W);
     return 0;
 }
 
 /* One facet's contribution (complex value and bin position) for tests:
    out = {re, im, p}. */
-void or_contribution(const or_scene *s, int n, int c, int64_t f, const double state[3], double *out)
+void or_contribution(const or_scene *s, int n, int c, int64_t f, const double state[8], double *out)
 {
     or_pulse g;
     or_pulse_state(s, n, c, &g);
@@ -592,24 +835,18 @@ int or_adjoint(const or_scene *s, int n_list, const int *pulses, const double *r
     int nc = s->n_channels, nr = s->n_range;
     int64_t nf = (int64_t)s->nx * s->ny;
     int ncell = s->ncx * s->ncy;
-    int nw = (s->static_surface ? 0 : s->n_omega * s->n_theta);
-    double *kx = NULL, *ky = NULL, *om = NULL, *amp = NULL, *ph = NULL;
-    if (nw > 0) {
-        kx = malloc(sizeof(double) * nw); ky = malloc(sizeof(double) * nw);
-        om = malloc(sizeof(double) * nw); amp = malloc(sizeof(double) * nw);
-        ph = malloc(sizeof(double) * nw);
-        or_wave_table(s, kx, ky, om, amp, ph);
-    }
+    or_waves W;
+    waves_build(s, &W);
     double lambda = OR_C / s->f0;
     double k0 = 2.0 * OR_PI / lambda;
-    double *st = malloc(sizeof(double) * 3 * nf);
+    double *st = malloc(sizeof(double) * 8 * nf);
     double r0[OR_MAXC];
     for (int c = 0; c < nc; ++c) r0[c] = or_range_start(s, c);
     /* per-channel partial gradients, summed in channel order at the end */
     double *part = calloc((size_t)nc * ncell * 3, sizeof(double));
     for (int i = 0; i < n_list; ++i) {
         int n = pulses[i];
-        or_facet_states(s, n, nw, kx, ky, om, amp, ph, st);
+        facet_states_w(s, &W, n, st);
 #pragma omp parallel for schedule(dynamic, 1)
         for (int c = 0; c < nc; ++c) {
             or_pulse g;
@@ -617,7 +854,8 @@ int or_adjoint(const or_scene *s, int n_list, const int *pulses, const double *r
             const double *row = resid + ((int64_t)c * n_list + i) * nr * 2;
             double *pc = part + (size_t)c * ncell * 3;
             for (int64_t f = 0; f < nf; ++f) {
-                double state[3] = {st[f], st[nf + f], st[2 * nf + f]};
+                double state[8];
+                for (int k = 0; k < 8; ++k) state[k] = st[k * nf + f];
                 double sre, sim, p, sx, sy;
                 int cell;
                 contribution_full(s, &g, n, c, f, state, r0[c], &sre, &sim, &p, &sx, &sy, &cell);
@@ -660,6 +898,6 @@ int or_adjoint(const or_scene *s, int n_list, const int *pulses, const double *r
         }
     free(part);
     free(st);
-    free(kx); free(ky); free(om); free(amp); free(ph);
+    waves_free(&W);
     return 0;
 }
