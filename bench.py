@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-scene batched measurement")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the timing of the surface and scattering variants")
     return ap.parse_args()
 
 
@@ -340,6 +342,8 @@ def main():
         line["adjoint"] = measure_adjoint(args, stream, flush)
     if prec == harm.HARM_PREC_MIXED and not args.no_batched:
         line["batched"] = measure_batched(args, stream)
+    if prec == harm.HARM_PREC_MIXED and not args.no_variants:
+        line["variants"] = measure_variants(args, stream, flush)
     if not args.no_cpu:
         cpu = run_oracle_sample(desc, args.cpu_pulses)
         # IQ error of the GPU path on the sampled pulses
@@ -446,24 +450,72 @@ def measure_batched(args, stream):
             "scene_create_s": create_s, "tune_s": tune_s}
 
 
+def measure_variants(args, stream, flush):
+    """The surface and scattering variants of Sec. III on one mid-size scene
+    (2 km x 1 km, 512 pulses, 6 channels, 4096 range samples; 1.536e9
+    contributions): device time of harm_echo_accumulate per variant (one warm-up,
+    then the mean of two timed runs, L2 flushed before each), and the ratio to
+    the plain scene."""
+    import torch
+    from paper_2405_09938_b300 import harm
+    base = hs.ati_scene(n_pulses=512, nx=1000, ny=500, n_range=4096)
+    variants = {
+        "plain": base,
+        "ar1_doppler": hs.ar1_speckle(base, tau_s=0.03, doppler_hz=12.0, epoch_pulses=8),
+        "uv_grids": hs.uv_patterns(base),
+        "hetero_512m": hs.hetero_sea(base, tile_m=512.0),
+        "cwm": hs.choppy(base),
+        "all": hs.uv_patterns(hs.choppy(hs.hetero_sea(
+            hs.ar1_speckle(base, tau_s=0.03, doppler_hz=12.0, epoch_pulses=8), tile_m=512.0))),
+    }
+    nc, npul, nr = len(base["rx"]), base["n_pulses"], base["n_range"]
+    iq = torch.empty((nc, npul, nr), dtype=torch.complex64, device="cuda")
+    units = hs.n_contributions(base)
+    out = {"workload": "ati_2x1km_512p_6ch", "contributions": units}
+    for name, d in variants.items():
+        scene = harm.harm_scene_create(d, harm.HARM_PREC_MIXED, stream)
+        times = []
+        for i in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            harm.harm_echo_accumulate(scene, 0, npul, iq)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if i > 0:
+                times.append(a.elapsed_time(b))
+        harm.harm_scene_sync(scene)
+        scene.close()
+        ms = statistics.mean(times)
+        out[name] = {"ms": ms, "value": units / (ms * 1e-3)}
+    for name in variants:
+        out[name]["vs_plain"] = out["plain"]["ms"] / out[name]["ms"]
+    del iq
+    torch.cuda.empty_cache()
+    return out
+
+
 def _launches_per_step(desc, prec, np_step):
     from paper_2405_09938_b300 import harm
     if prec == harm.HARM_PREC_MIXED:
-        batches = math.ceil(np_step / 32) + 1
+        batches = math.ceil(np_step / 128) + 1
         return max(1, math.ceil(batches / 65535))
     return max(1, math.ceil(np_step / 65535))
 
 
 def _scene_table_bytes(desc, prec):
+    """Bytes harm_scene_create uploads: pulse and receive states, wave tables,
+    u-v grid descriptors and the flag words."""
     from paper_2405_09938_b300 import harm
     nw = desc["n_omega"] * desc["n_theta"]
     npul, nc, nx, ny = desc["n_pulses"], len(desc["rx"]), desc["nx"], desc["ny"]
     pulse = npul * (8 * 2 + 8 * 10) + npul * nc * (8 * 10 + 16)
     if prec == harm.HARM_PREC_MIXED:
-        waves = nw * (nx + ny) * 8 + math.ceil(npul / 32) * nw * 15 * 8 + npul * 4 + nw * 24
+        nf = 8 if desc.get("cwm") else 3
+        waves = nw * (nx + ny) * 8 + math.ceil(npul / 128) * nw * nf * 6 * 8 + npul * 4 + nw * 32
     else:
-        waves = nw * (nx + ny + npul) * 16 + nw * 24
-    return pulse + waves + 16
+        waves = nw * (nx + ny + npul) * 16 + nw * 32
+    return pulse + waves + (1 + nc) * 56 + 16
 
 
 if __name__ == "__main__":

@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define HARM_ABI_VERSION 1u
+#define HARM_ABI_VERSION 2u
 #define HARM_MAX_CHANNELS 16
 
 typedef enum {
@@ -69,7 +69,9 @@ typedef struct {
 
 /* Scene, instrument and acquisition descriptor (the inputs of Sec. II-B: instrument,
    geometry, acquisition mode and geophysical scene). All fields are copied by
-   harm_scene_create; the rx array may be freed afterwards. */
+   harm_scene_create; the rx and hetero_* arrays may be freed afterwards.
+   Version 1 descriptors (abi_version = 1, struct_size = offsetof(harm_scene_desc,
+   speckle_tau_s)) are accepted and run with every version-2 variant off. */
 typedef struct {
     uint32_t abi_version;   /* HARM_ABI_VERSION */
     uint32_t struct_size;   /* sizeof(harm_scene_desc) */
@@ -101,6 +103,23 @@ typedef struct {
     int32_t taps;           /* 1 (Eq. 17 box) or 8 (Kaiser-windowed sinc) */
     double kaiser_beta;     /* Kaiser window beta for taps = 8 */
     int32_t precision;      /* harm_precision */
+    /* ---- abi_version >= 2: surface and scattering variants (Sec. III) ---- */
+    double speckle_tau_s;   /* correlation time tau_s of the order-1 autoregressive
+                               speckle (Eq. 10): s_e = beta s_(e-1) + sqrt(1 - beta^2) w_e
+                               between epochs, beta = exp(-epoch duration / tau_s);
+                               0 = independent epochs */
+    double speckle_doppler_hz; /* intra-facet Doppler shift f_s of Eq. 7 (uniform):
+                               the speckle carries exp(2 i pi f_s t_n) */
+    int32_t cwm;            /* 1: Choppy Wave Model -- facets move horizontally along
+                               the waves' orbits (Sec. III); 0: linear surface */
+    int32_t hetero_ncx;     /* heterogeneous sea state (Eq. 1, 2): corner grid of the */
+    int32_t hetero_ncy;     /* TL tiles, corner (cx, cy) at the patch corner + (cx, cy) L;
+                               0 = homogeneous. Needs (ncx - 1) L >= nx facet_m and
+                               (ncy - 1) L >= ny facet_m, at most 1024 corners. */
+    double hetero_tile_m;   /* TL tile size L */
+    const double *hetero_u10;          /* [ncy][ncx] wind speed of corner spectrum S_i (host) */
+    const double *hetero_wind_dir_rad; /* [ncy][ncx] wind direction of S_i (host); the NRCS
+                                          wind term keeps wind_dir_rad */
 } harm_scene_desc;
 
 typedef struct harm_scene harm_scene; /* opaque, owned by the library */
@@ -137,10 +156,27 @@ harm_status harm_scene_query(const harm_scene *scene, harm_scene_info *info);
 harm_status harm_scene_set_cells(harm_scene *scene, int32_t ncx, int32_t ncy, double cell_m,
                                  const double *sigma0_dev, const double *uv_dev);
 
-/* Facet generator (Sec. III linear surface, Sec. IV-B "generate the surface"):
-   writes (eta, eta_x, eta_y) of every facet for pulses [n0, n0 + np) at the
-   bounce time of each pulse, to state_dev laid out [np][3][n_facets], in double
-   for HARM_PREC_FP64 scenes and in float for HARM_PREC_MIXED scenes.
+/* Antenna gain from a u-v grid (Sec. III-B: patterns given in any form are
+   converted to u-v grids and looked up per facet and pulse) in place of the
+   analytic sinc^2 pattern. antenna = -1 for the transmitter, 0 .. n_channels - 1
+   for a receive channel. The grid holds complex gains (field weights) at
+   direction cosines u = u0 + i du along the antenna's azimuth axis and
+   v = v0 + j dv along its elevation axis: gain_host[j][i] interleaved (re, im)
+   doubles, nv x nu nodes, in HOST memory, copied into the scene (double for FP64
+   scenes, float for mixed ones). Between nodes the gain is bilinear; outside the
+   grid it is zero. gain_host = NULL removes the grid (back to sinc^2). nu, nv in
+   2 .. 65536, du, dv > 0. Synchronous with respect to the scene's stream.
+   Errors: HARM_E_INVALID, HARM_E_OOM, HARM_E_CUDA. */
+harm_status harm_scene_set_pattern(harm_scene *scene, int32_t antenna, int32_t nu, int32_t nv, double u0, double du,
+                                   double v0, double dv, const double *gain_host);
+
+/* Facet generator (Sec. III surface, Sec. IV-B "generate the surface"): writes
+   the state of every facet for pulses [n0, n0 + np) at the bounce time of each
+   pulse, to state_dev laid out [np][F][n_facets], in double for HARM_PREC_FP64
+   scenes and in float for HARM_PREC_MIXED scenes. F = 3 fields (eta, eta_x,
+   eta_y) for the linear surface; F = 8 with the Choppy Wave Model: (eta, eta_x,
+   eta_y, D_x, D_y, dD_x/dx, dD_x/dy, dD_y/dy), D the horizontal displacement and
+   every derivative taken with respect to the rest position.
    Errors: HARM_E_INVALID for an out-of-range pulse window or NULL pointer. */
 harm_status harm_facets_generate(harm_scene *scene, int32_t n0, int32_t np, void *state_dev);
 
@@ -170,7 +206,10 @@ typedef struct harm_batch harm_batch; /* opaque, owned by the library */
 
 /* Group n_scenes mixed-precision scenes (same device, same channel count, same
    taps and Kaiser beta) into one batched forward launch on the first scene's
-   stream. The batch keeps pointers to the scenes: they must outlive it. The work
+   stream. The batch keeps pointers to the scenes: they must outlive it, and it
+   copies their launch arguments (cells, u-v grids) when it is created, so a
+   scene changed afterwards needs a new batch. All scenes share the surface model
+   (cwm) and the pattern kind (with or without u-v grids). The work
    list is every (scene, 32 x rows facet tile, 32-pulse batch) item over the full
    burst of every scene, largest scenes first. Errors: HARM_E_INVALID (NULL,
    n_scenes < 1, mixed devices, channel counts or tap settings),

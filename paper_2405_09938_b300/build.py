@@ -5,6 +5,7 @@ shared library is written next to this file, so it travels with the source tree.
 """
 from __future__ import annotations
 
+import concurrent.futures
 import os
 import shutil
 import subprocess
@@ -15,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libharm.so")
-SOURCES = ["harm_scene.cu", "harm_dispatch.cu", "harm_batch.cu", "harm_noalloc.cu", "echo_fp64.cu", "echo_mixed.cu"]
+SOURCES = ["harm_scene.cu", "harm_dispatch.cu", "harm_batch.cu", "harm_noalloc.cu", "echo_fp64.cu", "echo_mixed.cu",
+           "echo_mixed_cwm.cu", "echo_mixed_lut.cu", "echo_mixed_cwm_lut.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -49,16 +51,20 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                     "-I" + INCLUDE, "-I" + CSRC] + list(extra)
     if verbose:
         flags += ["-Xptxas", "-v"]
-    objs = []
-    for src in SOURCES:
-        obj = os.path.join(objdir, src.replace(".cu", ".o"))
+    objs = [os.path.join(objdir, src.replace(".cu", ".o")) for src in SOURCES]
+
+    def compile_one(src, obj):
         cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj] + flags
-        r = subprocess.run(cmd, capture_output=True, text=True)
+        return src, subprocess.run(cmd, capture_output=True, text=True)
+
+    # the translation units are independent: compile them in parallel
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 1)) as ex:
+        results = list(ex.map(lambda a: compile_one(*a), zip(SOURCES, objs)))
+    for src, r in results:
         if verbose or r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s" % src)
-        objs.append(obj)
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

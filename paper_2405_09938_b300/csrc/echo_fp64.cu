@@ -2,11 +2,13 @@
 // double precision (the reference GPU form the mixed path is measured against).
 //
 // Work decomposition: one CTA = a 16 x 16 facet tile x one pulse; one thread per
-// facet. Each thread synthesises its facet's height and slopes (linear waves,
+// facet. Each thread synthesises its facet's state (linear waves or the Choppy
+// Wave Model, one wave set or the four corner sets of a heterogeneous sea state,
 // separable phasors), then for every channel forms the contribution of Eq. 3 /
-// Eq. 16 and spreads it over the range bins (Eq. 17 box or 8-tap Kaiser-sinc)
-// into a shared-memory range tile of the CTA. The tile is flushed to the IQ with
-// one atomic per bin and channel.
+// Eq. 16 (analytic or u-v grid gains, AR(1) speckle of Eq. 10 with the Doppler
+// rotation of Eq. 7) and spreads it over the range bins (Eq. 17 box or 8-tap
+// Kaiser-sinc) into a shared-memory range tile of the CTA. The tile is flushed to
+// the IQ with one atomic per bin and channel.
 #include <cuda_runtime.h>
 
 #include "harm_internal.cuh"
@@ -40,29 +42,91 @@ __device__ __forceinline__ double gain_d(const AntState &s, double laz, double l
     return sa * sa * se * se;
 }
 
-// Height and slopes at rest position (ix, iy), pulse n, from the separable
-// tables: eta = Re sum_m Ex[m,ix] Ey[m,iy] T[m,n]; slopes = -k Im(...).
-__device__ void surface_d(const DevScene &S, int ix, int iy, int n, double &eta, double &ex, double &ey)
+// Complex gain from a u-v grid (Sec. III-B): bilinear between the four nodes
+// around (u, v), zero outside the grid.
+__device__ double2 lut_gain_d(const PatLut &L, double u, double v)
 {
-    eta = ex = ey = 0.0;
-    const double2 *px = S.ex + ix;
-    const double2 *py = S.ey + iy;
-    const double2 *pt = S.tt + n;
+    const double fu = (u - L.u0) * L.inv_du, fv = (v - L.v0) * L.inv_dv;
+    if (!(fu >= 0.0 && fu <= (double)(L.nu - 1) && fv >= 0.0 && fv <= (double)(L.nv - 1)))
+        return make_double2(0.0, 0.0);
+    const int iu = min((int)floor(fu), L.nu - 2), iv = min((int)floor(fv), L.nv - 2);
+    const double a = fu - iu, b = fv - iv;
+    const double2 *g = L.g64 + (size_t)iv * L.nu + iu;
+    const double2 g00 = g[0], g10 = g[1], g01 = g[L.nu], g11 = g[L.nu + 1];
+    const double w00 = (1.0 - a) * (1.0 - b), w10 = a * (1.0 - b), w01 = (1.0 - a) * b, w11 = a * b;
+    return make_double2(w00 * g00.x + w10 * g10.x + w01 * g01.x + w11 * g11.x,
+                        w00 * g00.y + w10 * g10.y + w01 * g01.y + w11 * g11.y);
+}
+
+// Gain of antenna slot (0 = transmitter, 1 + c = receive channel c) for unit
+// direction d: the u-v grid when one is set, else the analytic pattern.
+__device__ __forceinline__ double2 antenna_gain_d(const DevScene &S, int slot, const AntState &a, double laz,
+                                                  double lel, const double d[3])
+{
+    if (S.lut_mask & (1u << slot)) return lut_gain_d(S.luts[slot], dot3(d, a.a), dot3(d, a.e));
+    return make_double2(gain_d(a, laz, lel, S.inv_lambda, d), 0.0);
+}
+
+// Fields of one wave set q at rest position (ix, iy), pulse n, added with weight
+// w: with Q E = a e^{i(k.x + phi)} e^{-i omega t_s} = (vr, vi),
+// eta = vr, slopes -k vi, and for the Choppy Wave Model the horizontal
+// displacement -(k / |k|) vi and its gradient -(k_i k_j / |k|) vr.
+__device__ void wave_set_d(const DevScene &S, int q, int ix, int iy, int n, double w, double st[8])
+{
+    const size_t base = (size_t)q * S.nw;
+    const double2 *px = S.ex + base * S.nx + ix;
+    const double2 *py = S.ey + base * S.ny + iy;
+    const double2 *pt = S.tt + base * S.np_total + n;
     for (int m = 0; m < S.nw; ++m) {
         double2 a = __ldg(px + (size_t)m * S.nx);
         double2 b = __ldg(py + (size_t)m * S.ny);
         double2 t = __ldg(pt + (size_t)m * S.np_total);
         double qr = a.x * b.x - a.y * b.y;
         double qi = a.x * b.y + a.y * b.x;
-        double vr = qr * t.x - qi * t.y;
-        double vi = qr * t.y + qi * t.x;
-        eta += vr;
-        ex -= __ldg(S.kx + m) * vi;
-        ey -= __ldg(S.ky + m) * vi;
+        double vr = w * (qr * t.x - qi * t.y);
+        double vi = w * (qr * t.y + qi * t.x);
+        const double kx = __ldg(S.kx + base + m), ky = __ldg(S.ky + base + m);
+        st[0] += vr;
+        st[1] -= kx * vi;
+        st[2] -= ky * vi;
+        if (S.cwm) {
+            const double ik = 1.0 / __ldg(S.kn + base + m);
+            const double ux = kx * ik, uy = ky * ik;
+            st[3] -= ux * vi;
+            st[4] -= uy * vi;
+            st[5] -= ux * kx * vr;
+            st[6] -= ux * ky * vr;
+            st[7] -= uy * ky * vr;
+        }
     }
 }
 
-// Intra-facet speckle (Eq. 7 with f_s = 0): Box-Muller on Philox words,
+// Facet state (8 fields; the last 5 zero without the Choppy Wave Model) at rest
+// position (ix, iy), pulse n. A heterogeneous sea state sums the wave sets of
+// the four corners of the facet's TL tile with the weights of Eq. 2 (Eq. 1).
+__device__ void facet_state_d(const DevScene &S, int ix, int iy, int n, double st[8])
+{
+    for (int q = 0; q < 8; ++q) st[q] = 0.0;
+    if (S.static_surface || S.nw == 0) return;
+    if (S.het_ncx > 0) {
+        const double x = (ix + 0.5 - 0.5 * S.nx) * S.dx, y = (iy + 0.5 - 0.5 * S.ny) * S.dx;
+        const int tx = min(max((int)floor((x - S.het_x0) / S.het_l), 0), S.het_ncx - 2);
+        const int ty = min(max((int)floor((y - S.het_y0) / S.het_l), 0), S.het_ncy - 2);
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                const int cx = tx + dx, cy = ty + dy;
+                const double wx = fabs(S.het_x0 + cx * S.het_l - x) / S.het_l;
+                const double wy = fabs(S.het_y0 + cy * S.het_l - y) / S.het_l;
+                const double v = 1.0 - wx - wy + wx * wy;
+                if (!(v > 0.0)) continue;
+                wave_set_d(S, cy * S.het_ncx + cx, ix, iy, n, sqrt(v), st);
+            }
+    } else {
+        wave_set_d(S, 0, ix, iy, n, 1.0, st);
+    }
+}
+
+// Intra-facet speckle (Eq. 7 at f_s = 0): Box-Muller on Philox words,
 // R, I ~ N(0, 1/2).
 __device__ __forceinline__ void speckle_d(uint64_t seed, uint32_t f, uint32_t epoch, double &zr, double &zi)
 {
@@ -74,6 +138,23 @@ __device__ __forceinline__ void speckle_d(uint64_t seed, uint32_t f, uint32_t ep
     sincospi(2.0 * u2, &s, &c);
     zr = rad * c;
     zi = rad * s;
+}
+
+// Speckle under the order-1 autoregressive model of Eq. 10: s_0 = w_0,
+// s_e = beta s_(e-1) + sqrt(1 - beta^2) w_e, run from epoch 0.
+__device__ void speckle_ar1_d(const DevScene &S, uint32_t f, uint32_t epoch, double &zr, double &zi)
+{
+    if (S.spk_beta == 0.0) {
+        speckle_d(S.speckle_seed, f, epoch, zr, zi);
+        return;
+    }
+    speckle_d(S.speckle_seed, f, 0u, zr, zi);
+    for (uint32_t e = 1; e <= epoch; ++e) {
+        double wr, wi;
+        speckle_d(S.speckle_seed, f, e, wr, wi);
+        zr = S.spk_beta * zr + S.spk_q * wr;
+        zi = S.spk_beta * zi + S.spk_q * wi;
+    }
 }
 
 // Kaiser window I0(beta sqrt(1 - (x/4)^2)) / I0(beta) from its power series in
@@ -115,12 +196,11 @@ __global__ void __launch_bounds__(256) generate_f64_kernel(DevScene S, int n0, i
     int n = nfirst + blockIdx.y;
     if (f >= nf) return;
     int ix = (int)(f % S.nx), iy = (int)(f / S.nx);
-    double eta = 0, ex = 0, ey = 0;
-    if (!S.static_surface && S.nw > 0) surface_d(S, ix, iy, n, eta, ex, ey);
-    double *o = state + (size_t)(n - n0) * 3 * nf;
-    o[f] = eta;
-    o[nf + f] = ex;
-    o[2 * nf + f] = ey;
+    double st[8];
+    facet_state_d(S, ix, iy, n, st);
+    const int nfl = S.cwm ? 8 : 3;
+    double *o = state + (size_t)(n - n0) * nfl * nf;
+    for (int q = 0; q < nfl; ++q) o[q * nf + f] = st[q];
 }
 
 template <int TAPS, typename OutT>
@@ -155,10 +235,18 @@ __global__ void __launch_bounds__(256) accumulate_f64_kernel(DevScene S, int n0,
 
     if (valid) {
         const uint32_t f = (uint32_t)iy * (uint32_t)S.nx + (uint32_t)ix;
-        double eta = 0, sx = 0, sy = 0;
-        if (!S.static_surface && S.nw > 0) surface_d(S, ix, iy, n, eta, sx, sy);
-        const double x[3] = {(ix + 0.5 - 0.5 * S.nx) * S.dx, (iy + 0.5 - 0.5 * S.ny) * S.dx, eta};
+        double st[8];
+        facet_state_d(S, ix, iy, n, st);
+        // rest position, moved by the horizontal displacement (CWM) and lifted to eta
+        const double xb = (ix + 0.5 - 0.5 * S.nx) * S.dx, yb = (iy + 0.5 - 0.5 * S.ny) * S.dx;
+        const double x[3] = {xb + st[3], yb + st[4], st[0]};
         const double xx = dot3(x, x);
+        // normal: cross product of the displaced surface's tangents
+        // (1 + dDx/dx, dDx/dy, eta_x) and (dDx/dy, 1 + dDy/dy, eta_y)
+        const double nv[3] = {st[6] * st[2] - st[1] * (1.0 + st[7]), st[1] * st[6] - (1.0 + st[5]) * st[2],
+                              (1.0 + st[5]) * (1.0 + st[7]) - st[6] * st[6]};
+        const double nlen = sqrt(dot3(nv, nv));
+        const double area = S.area * fmax(nv[2], 0.0);
 
         // transmit leg: range offset from the scene-centre range in the stable
         // form (|x|^2 - 2 P.x) / (r + R), unit vector, pattern gain
@@ -166,12 +254,12 @@ __global__ void __launch_bounds__(256) accumulate_f64_kernel(DevScene S, int n0,
         double rt = sqrt(dot3(dtv, dtv));
         double delt = (xx - 2.0 * dot3(P.tx.p, x)) / (rt + P.tx.rref);
         double ut[3] = {dtv[0] / rt, dtv[1] / rt, dtv[2] / rt};
-        double gt = gain_d(P.tx, S.tx_laz, S.tx_lel, S.inv_lambda, ut);
+        const double2 gt = antenna_gain_d(S, 0, P.tx, S.tx_laz, S.tx_lel, ut);
 
         double base = S.sigma0_base, cu = S.cur_u, cv = S.cur_v;
         if (S.cell_sigma0 || S.cell_uv) {
-            int cx = (int)floor((x[0] + 0.5 * S.nx * S.dx) / S.cell);
-            int cy = (int)floor((x[1] + 0.5 * S.ny * S.dx) / S.cell);
+            int cx = (int)floor((xb + 0.5 * S.nx * S.dx) / S.cell);
+            int cy = (int)floor((yb + 0.5 * S.ny * S.dx) / S.cell);
             cx = min(max(cx, 0), S.ncx - 1);
             cy = min(max(cy, 0), S.ncy - 1);
             int ci = cy * S.ncx + cx;
@@ -183,8 +271,8 @@ __global__ void __launch_bounds__(256) accumulate_f64_kernel(DevScene S, int n0,
         }
         uint32_t epoch = S.epoch_pulses > 0 ? (uint32_t)(n / S.epoch_pulses) : 0u;
         double zr, zi;
-        speckle_d(S.speckle_seed, f, epoch, zr, zi);
-        const double nlen = sqrt(1.0 + sx * sx + sy * sy);
+        speckle_ar1_d(S, f, epoch, zr, zi);
+        const double fd_phase = 2.0 * kPi * S.fd_hz * P.t;
 
         for (int c = 0; c < S.nc; ++c) {
             const RxState &R = S.rx[(size_t)n * S.nc + c];
@@ -192,23 +280,25 @@ __global__ void __launch_bounds__(256) accumulate_f64_kernel(DevScene S, int n0,
             double rr = sqrt(dot3(drv, drv));
             double delr = (xx - 2.0 * dot3(R.rx.p, x)) / (rr + R.rx.rref);
             double ur[3] = {drv[0] / rr, drv[1] / rr, drv[2] / rr};
-            double gr = gain_d(R.rx, S.rx_laz[c], S.rx_lel[c], S.inv_lambda, ur);
+            const double2 gr = antenna_gain_d(S, 1 + c, R.rx, S.rx_laz[c], S.rx_lel[c], ur);
 
             double sig = base;
             if (!S.static_surface) {
                 double q[3] = {-(ut[0] + ur[0]), -(ut[1] + ur[1]), -(ut[2] + ur[2])};
                 double qh = sqrt(q[0] * q[0] + q[1] * q[1]);
                 double cphi = qh > 0.0 ? (S.wcos * q[0] + S.wsin * q[1]) / qh : 0.0;
-                double nq = q[2] - sx * q[0] - sy * q[1];
+                double nq = dot3(nv, q);
                 double tilt = fmax(nq, 0.0) / (nlen * q[2]);
                 sig = base * (1.0 + S.wind_mod * cphi) * tilt;
             }
-            double amp = sqrt(sig * S.area) * gt * gr * (P.tx.rref / rt) * (R.rx.rref / rr);
+            double amp = sqrt(sig * area) * (P.tx.rref / rt) * (R.rx.rref / rr);
             double vc = cu * (ut[0] + ur[0]) + cv * (ut[1] + ur[1]);
-            double phase = R.psi - S.k0 * (delt + delr + vc * P.t);
+            double phase = R.psi - S.k0 * (delt + delr + vc * P.t) + fd_phase;
             double sp, cp;
             sincos(phase, &sp, &cp);
-            double ar = amp * zr, ai = amp * zi;
+            // field weight G_t G_r (complex for u-v grids) times the speckle
+            const double gre = gt.x * gr.x - gt.y * gr.y, gim = gt.x * gr.y + gt.y * gr.x;
+            double ar = amp * (zr * gre - zi * gim), ai = amp * (zr * gim + zi * gre);
             double vr = ar * cp - ai * sp;
             double vi = ar * sp + ai * cp;
             double p = R.p_ref + (delt + delr) * S.inv_dr;

@@ -23,6 +23,7 @@ struct harm_batch {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int device = 0;
     int nc = 0, taps = 8;
+    int variant = 0;
     int ctas = 0;
     std::vector<int> ty;        // tile rows by scene
     std::vector<int> order;     // processing order (largest first)
@@ -126,6 +127,7 @@ harm::BatchLaunch launch_desc(harm_batch *b, int total)
     L.nc = b->nc;
     L.taps = b->taps;
     L.ctas = b->ctas;
+    L.variant = b->variant;
     return L;
 }
 
@@ -178,6 +180,8 @@ harm_status harm_batch_create(harm_scene *const *scenes, int32_t n, harm_batch *
             return fail(HARM_E_INVALID, "scenes must have the same number of channels");
         if (sc->desc.taps != scenes[0]->desc.taps || sc->desc.kaiser_beta != scenes[0]->desc.kaiser_beta)
             return fail(HARM_E_INVALID, "scenes must share taps and kaiser_beta");
+        if (harm::batch_variant(sc) != harm::batch_variant(scenes[0]))
+            return fail(HARM_E_INVALID, "scenes must share the surface model (CWM) and the pattern kind (u-v grids)");
     }
     harm_batch *b = new (std::nothrow) harm_batch;
     if (!b) return fail(HARM_E_OOM, "host allocation failed");
@@ -195,7 +199,8 @@ harm_status harm_batch_create(harm_scene *const *scenes, int32_t n, harm_batch *
     }
     b->nc = scenes[0]->desc.n_channels;
     b->taps = scenes[0]->desc.taps;
-    b->ctas = harm::batch_ctas(b->device);
+    b->variant = harm::batch_variant(scenes[0]);
+    b->ctas = harm::batch_ctas(b->device, b->variant);
     b->ty.assign(n, 16);
     b->order.resize(n);
     for (int s = 0; s < n; ++s) b->order[s] = s;

@@ -110,51 +110,65 @@ void fit_sinc2(float out[kSincDeg + 1])
 
 }  // namespace
 
-harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps, const std::vector<Wave> &waves)
+harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps, const WaveSets &W)
 {
     const harm_scene_desc &d = s->desc;
     MixedTables &M = s->mixed;
     const int nx = d.nx, ny = d.ny, np = d.n_pulses;
-    const int nw = (int)waves.size();
+    const int nw = W.nw, nsets = W.n_sets;
+    const int nf = d.cwm ? 8 : 3;
     M.nb = mixed_batch_pulses();
     M.n_batches = (np + M.nb - 1) / M.nb;
-    std::vector<float2> ex((size_t)std::max(nw, 1) * nx), ey((size_t)std::max(nw, 1) * ny);
-    for (int m = 0; m < nw; ++m) {
-        for (int ix = 0; ix < nx; ++ix) {
-            double a = waves[m].kx * (ix + 0.5 - 0.5 * nx) * d.facet_m;
-            ex[(size_t)m * nx + ix] = make_float2((float)std::cos(a), (float)std::sin(a));
+    M.nf = nf;
+    const size_t nsw = (size_t)nsets * std::max(nw, 1);
+    std::vector<float2> ex(nsw * nx), ey(nsw * ny);
+    for (int q = 0; q < nsets; ++q)
+        for (int m = 0; m < nw; ++m) {
+            const Wave &w = W.at(q, m);
+            const size_t qm = (size_t)q * nw + m;
+            for (int ix = 0; ix < nx; ++ix) {
+                double a = w.kx * (ix + 0.5 - 0.5 * nx) * d.facet_m;
+                ex[qm * nx + ix] = make_float2((float)std::cos(a), (float)std::sin(a));
+            }
+            for (int iy = 0; iy < ny; ++iy) {
+                double a = w.ky * (iy + 0.5 - 0.5 * ny) * d.facet_m + w.ph;
+                ey[qm * ny + iy] = make_float2((float)(w.amp * std::cos(a)), (float)(w.amp * std::sin(a)));
+            }
         }
-        for (int iy = 0; iy < ny; ++iy) {
-            double a = waves[m].ky * (iy + 0.5 - 0.5 * ny) * d.facet_m + waves[m].ph;
-            ey[(size_t)m * ny + iy] =
-                make_float2((float)(waves[m].amp * std::cos(a)), (float)(waves[m].amp * std::sin(a)));
-        }
-    }
     // Taylor tables: E_{w,o} = e^{-i omega t_c} (-i omega)^o / o! about the batch
-    // centre t_c; fields eta (E), eta_x (i kx E), eta_y (i ky E).
+    // centre t_c, times the complex factor c_f of each field (state field f =
+    // Re(c_f Q E) for the component phasor Q): eta (1), eta_x (i kx), eta_y (i ky),
+    // and with the Choppy Wave Model D_x (i kx/k), D_y (i ky/k), dD_x/dx (-kx^2/k),
+    // dD_x/dy (-kx ky/k), dD_y/dy (-ky^2/k).
     std::vector<float> tau(np);
-    std::vector<float2> wt((size_t)M.n_batches * std::max(nw, 1) * 3 * kOrders);
+    std::vector<float2> wt((size_t)M.n_batches * nsw * nf * kOrders);
     for (int b = 0; b < M.n_batches; ++b) {
         int first = b * M.nb, last = std::min(np, first + M.nb) - 1;
         double tc = 0.5 * (ps[first].ts + ps[last].ts);
         for (int n = first; n <= last; ++n) tau[n] = (float)(ps[n].ts - tc);
-        for (int m = 0; m < nw; ++m) {
-            double om = waves[m].om;
-            double er = std::cos(-om * tc), ei = std::sin(-om * tc);
-            for (int o = 0; o < kOrders; ++o) {
-                if (o > 0) {
-                    // multiply by (-i omega) / o
-                    double nr = om * ei / o, ni = -om * er / o;
-                    er = nr;
-                    ei = ni;
+        for (int q = 0; q < nsets; ++q)
+            for (int m = 0; m < nw; ++m) {
+                const Wave &w = W.at(q, m);
+                const double k = std::sqrt(w.kx * w.kx + w.ky * w.ky);
+                // c_f = (cr, ci)
+                const double cf[8][2] = {{1.0, 0.0},          {0.0, w.kx},          {0.0, w.ky},
+                                         {0.0, w.kx / k},     {0.0, w.ky / k},      {-w.kx * w.kx / k, 0.0},
+                                         {-w.kx * w.ky / k, 0.0}, {-w.ky * w.ky / k, 0.0}};
+                double er = std::cos(-w.om * tc), ei = std::sin(-w.om * tc);
+                for (int o = 0; o < kOrders; ++o) {
+                    if (o > 0) {
+                        // multiply by (-i omega) / o
+                        double nr = w.om * ei / o, ni = -w.om * er / o;
+                        er = nr;
+                        ei = ni;
+                    }
+                    const size_t base = ((((size_t)b * nsets + q) * nw + m) * nf) * kOrders + o;
+                    for (int f = 0; f < nf; ++f) {
+                        const double vr = cf[f][0] * er - cf[f][1] * ei, vi = cf[f][0] * ei + cf[f][1] * er;
+                        wt[base + (size_t)f * kOrders] = make_float2((float)vr, (float)vi);
+                    }
                 }
-                size_t base = (((size_t)b * nw + m) * 3) * kOrders + o;
-                wt[base] = make_float2((float)er, (float)ei);
-                // i k E = (-k Ei, k Er)
-                wt[base + kOrders] = make_float2((float)(-waves[m].kx * ei), (float)(waves[m].kx * er));
-                wt[base + 2 * kOrders] = make_float2((float)(-waves[m].ky * ei), (float)(waves[m].ky * er));
             }
-        }
     }
     fit_taps(s->dev, M.tap);
     fit_sinc2(M.sinc2);

@@ -36,6 +36,14 @@ struct RxState {
     double p_ref;   // (R_t + R_r - R0_c) / dr: bin position of the scene centre
 };
 
+// u-v gain grid of one antenna (device copy owned by the scene).
+struct PatLut {
+    int nu, nv;
+    double u0, inv_du, v0, inv_dv;
+    const double2 *g64;  // [nv][nu] (FP64 scenes)
+    const float2 *g32;   // [nv][nu] (mixed scenes)
+};
+
 // Scene constants passed by value to every kernel.
 struct DevScene {
     int nx, ny, nc, nr, np_total, nw, taps, static_surface, epoch_pulses;
@@ -59,6 +67,17 @@ struct DevScene {
     const double2 *ey;          // [nw][ny]   a e^{i phi} e^{i ky y}
     const double2 *tt;          // [nw][np_total] e^{-i omega t_s}
     unsigned int *flags;        // device error / overflow counters [4]
+    // variants of Sec. III
+    int cwm;                    // Choppy Wave Model: 8 state fields instead of 3
+    int n_sets;                 // wave sets: 1, or one per corner of a heterogeneous sea state
+    int het_ncx, het_ncy;       // corner grid (0 = homogeneous)
+    double het_l, het_x0, het_y0;  // TL tile size, position of corner (0, 0)
+    double spk_beta, spk_q;     // AR(1) speckle s_e = beta s_(e-1) + q w_e (beta = 0: independent)
+    int spk_terms;              // AR(1) terms kept when a pulse window starts mid-burst
+    double fd_hz;               // intra-facet Doppler shift f_s
+    unsigned int lut_mask;      // bit 0: transmitter grid, bit 1 + c: receive channel c grid
+    const PatLut *luts;         // [1 + nc] (device)
+    const double *kn;           // [n_sets][nw] |k| (CWM direction cosines of the waves)
 };
 
 // Mixed-precision tables (FP32 separable waves, Taylor time tables).

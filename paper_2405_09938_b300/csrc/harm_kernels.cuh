@@ -18,10 +18,11 @@ constexpr int kOrders = 6;      // Taylor orders in time: tau^0 .. tau^5
 struct MixedTables {
     int nb = 0;             // pulses per batch (time-Taylor expansion window)
     int n_batches = 0;
+    int nf = 3;             // state fields: 3 (linear surface) or 8 (Choppy Wave Model)
     int tile_x = 32, tile_y = 16;
-    const float2 *ex = nullptr;   // [nw][nx]          e^{i kx x}
-    const float2 *ey = nullptr;   // [nw][ny]          a e^{i phi} e^{i ky y}
-    const float2 *wt = nullptr;   // [n_batches][nw][3][kOrders] Taylor coefficients
+    const float2 *ex = nullptr;   // [n_sets][nw][nx]  e^{i kx x}
+    const float2 *ey = nullptr;   // [n_sets][nw][ny]  a e^{i phi} e^{i ky y}
+    const float2 *wt = nullptr;   // [n_batches][n_sets][nw][nf][kOrders] Taylor coefficients
     const float *tau = nullptr;   // [np_total] t_s(n) - t_centre(batch)
     float tap[8][kTapDeg + 1];    // Kaiser-sinc tap h(j - f), j = -3..4, monomials in t
     float sinc2[kSincDeg + 1];    // sinc^2(x) for |x| <= 1, monomials in t = 2 x^2 - 1
@@ -32,6 +33,10 @@ struct MixedTables {
 struct harm_scene {
     harm_scene_desc desc{};
     std::vector<harm_antenna> rx;
+    std::vector<double> het_u10, het_dir;  // corner spectra of a heterogeneous sea state
+    std::vector<harm::PatLut> luts;        // [1 + nc] u-v gain grids (host copy of the descriptors)
+    std::vector<void *> lut_mem;           // [1 + nc] device memory of each grid (or null)
+    harm::PatLut *luts_dev = nullptr;      // [1 + nc] descriptors on the device
     cudaStream_t stream = nullptr;
     int device = 0;
     harm::DevScene dev{};
@@ -48,8 +53,16 @@ struct Wave {
     double kx, ky, om, amp, ph;
 };
 
+// Wave sets of a scene: [n_sets][nw] components (one set for a homogeneous sea
+// state, one per corner of a heterogeneous one).
+struct WaveSets {
+    int n_sets = 1, nw = 0;
+    std::vector<Wave> w;
+    const Wave &at(int set, int m) const { return w[(size_t)set * nw + m]; }
+};
+
 harm_status build_scene_tables(harm_scene *s);
-harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps, const std::vector<Wave> &waves);
+harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps, const WaveSets &waves);
 
 cudaError_t launch_generate(harm_scene *s, int n0, int np, void *state);
 cudaError_t launch_accumulate(harm_scene *s, int n0, int np, void *iq, harm_dtype dtype);
@@ -75,11 +88,13 @@ struct BatchLaunch {
     unsigned int *counter;   // work counter (zeroed before the launch)
     const MixedTables *poly; // tap / sinc polynomials (shared)
     int n, total, nc, taps, ctas;
+    int variant;             // per-pulse code variant shared by the scenes (see batch_variant)
 };
 size_t batch_args_bytes();
 void batch_fill_args(const harm_scene *s, void *dst);
 int batch_tiles(const harm_scene *s, int ty);
-int batch_ctas(int device);
+int batch_variant(const harm_scene *s);  // surface model / pattern kind of the per-pulse code
+int batch_ctas(int device, int variant);
 cudaError_t batch_launch(const BatchLaunch &L, cudaStream_t st);
 
 cudaError_t launch_adjoint_mixed(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np,

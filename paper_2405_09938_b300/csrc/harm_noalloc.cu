@@ -86,6 +86,8 @@ extern "C" harm_status harm_batch_run_noalloc(harm_scene *const *scenes, int32_t
             return fail(HARM_E_INVALID, "scenes must have the same number of channels");
         if (sc->desc.taps != scenes[0]->desc.taps || sc->desc.kaiser_beta != scenes[0]->desc.kaiser_beta)
             return fail(HARM_E_INVALID, "scenes must share taps and kaiser_beta");
+        if (harm::batch_variant(sc) != harm::batch_variant(scenes[0]))
+            return fail(HARM_E_INVALID, "scenes must share the surface model (CWM) and the pattern kind (u-v grids)");
         cudaPointerAttributes a;
         if (cudaPointerGetAttributes(&a, iq_dev[s]) != cudaSuccess ||
             (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
@@ -152,7 +154,8 @@ extern "C" harm_status harm_batch_run_noalloc(harm_scene *const *scenes, int32_t
         L.total = h.start[n];
         L.nc = scenes[0]->desc.n_channels;
         L.taps = scenes[0]->desc.taps;
-        L.ctas = harm::batch_ctas(dev);
+        L.variant = harm::batch_variant(scenes[0]);
+        L.ctas = harm::batch_ctas(dev, L.variant);
         e = harm::batch_launch(L, stream);
     }
     if (e != cudaSuccess) {

@@ -5,6 +5,7 @@
 // n_waves x (nx + ny + n_pulses))); all per-facet work runs in the kernels.
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -130,13 +131,14 @@ double peak_omega(double u10, double fetch)
 
 // Linear-wave grid: log-spaced frequency bins on [0.7, 2.5] x peak (geometric
 // centres), equally spaced directions about the wind, cos^2s spreading,
-// amplitude from the spectral energy of each cell, Philox phase.
-std::vector<harm::Wave> wave_grid(const harm_scene_desc &d)
+// amplitude from the spectral energy of each cell, Philox phase (counter word 2
+// = word2: 0 for a homogeneous sea state, 1 + corner for a heterogeneous one).
+std::vector<harm::Wave> wave_grid(const harm_scene_desc &d, double u10, double wind_dir, uint32_t word2)
 {
     std::vector<harm::Wave> w;
     if (d.n_omega <= 0 || d.n_theta <= 0 || d.static_surface) return w;
     const double g = 9.80665;
-    double wp = peak_omega(d.u10, d.fetch_m);
+    double wp = peak_omega(u10, d.fetch_m);
     double lo = 0.7 * wp, ratio = 2.5 / 0.7;
     double dth = 2.0 * harm::kPi / d.n_theta;
     double s = d.spread_s;
@@ -145,14 +147,14 @@ std::vector<harm::Wave> wave_grid(const harm_scene_desc &d)
         double e0 = lo * std::pow(ratio, (double)i / d.n_omega);
         double e1 = lo * std::pow(ratio, (double)(i + 1) / d.n_omega);
         double om = std::sqrt(e0 * e1);
-        double sw = jonswap(om, d.u10, d.fetch_m, d.gamma);
+        double sw = jonswap(om, u10, d.fetch_m, d.gamma);
         double k = om * om / g;
         for (int j = 0; j < d.n_theta; ++j) {
             int m = i * d.n_theta + j;
             double rel = -harm::kPi + (j + 0.5) * dth;
-            double th = d.wind_dir_rad + rel;
+            double th = wind_dir + rel;
             double spread = norm * std::pow(std::cos(0.5 * rel), 2.0 * s);
-            harm::U32x4 r = harm::philox_stream(d.wave_seed, harm::kStreamWave, (uint32_t)m, 0u);
+            harm::U32x4 r = harm::philox_stream(d.wave_seed, harm::kStreamWave, (uint32_t)m, word2);
             harm::Wave v;
             v.kx = k * std::cos(th);
             v.ky = k * std::sin(th);
@@ -165,13 +167,55 @@ std::vector<harm::Wave> wave_grid(const harm_scene_desc &d)
     return w;
 }
 
-harm_status validate(const harm_scene_desc *d)
+// Every wave set of the scene: the scene's spectrum, or one per corner of a
+// heterogeneous sea state with the corner's wind speed and direction (Eq. 1).
+harm::WaveSets wave_sets(const harm_scene *s)
+{
+    const harm_scene_desc &d = s->desc;
+    harm::WaveSets W;
+    if (d.hetero_ncx > 0) {
+        W.n_sets = d.hetero_ncx * d.hetero_ncy;
+        for (int i = 0; i < W.n_sets; ++i) {
+            std::vector<harm::Wave> w = wave_grid(d, s->het_u10[i], s->het_dir[i], 1u + (uint32_t)i);
+            W.nw = (int)w.size();
+            W.w.insert(W.w.end(), w.begin(), w.end());
+        }
+    } else {
+        W.w = wave_grid(d, d.u10, d.wind_dir_rad, 0u);
+        W.nw = (int)W.w.size();
+    }
+    return W;
+}
+
+// Size of a version-1 descriptor: everything before the version-2 fields.
+constexpr size_t kDescV1Size = offsetof(harm_scene_desc, speckle_tau_s);
+
+// Copy a descriptor of either version into *out (version-2 fields zero for a
+// version-1 descriptor).
+harm_status normalize(const harm_scene_desc *d, harm_scene_desc *out)
 {
     if (!d) return fail(HARM_E_INVALID, "desc is NULL");
-    if (d->abi_version != HARM_ABI_VERSION)
-        return fail(HARM_E_INVALID, "abi_version %u, library is %u", d->abi_version, HARM_ABI_VERSION);
-    if (d->struct_size != sizeof(harm_scene_desc))
-        return fail(HARM_E_INVALID, "struct_size %u, library expects %zu", d->struct_size, sizeof(harm_scene_desc));
+    std::memset(out, 0, sizeof(*out));
+    if (d->abi_version == 1u) {
+        if (d->struct_size != kDescV1Size)
+            return fail(HARM_E_INVALID, "struct_size %u, a version-1 descriptor has %zu", d->struct_size, kDescV1Size);
+        std::memcpy(out, d, kDescV1Size);
+    } else if (d->abi_version == HARM_ABI_VERSION) {
+        if (d->struct_size != sizeof(harm_scene_desc))
+            return fail(HARM_E_INVALID, "struct_size %u, library expects %zu", d->struct_size, sizeof(harm_scene_desc));
+        std::memcpy(out, d, sizeof(*out));
+    } else {
+        return fail(HARM_E_INVALID, "abi_version %u, library is %u (accepts 1 and %u)", d->abi_version,
+                    HARM_ABI_VERSION, HARM_ABI_VERSION);
+    }
+    out->abi_version = HARM_ABI_VERSION;
+    out->struct_size = sizeof(harm_scene_desc);
+    return HARM_OK;
+}
+
+// Validate a normalized descriptor.
+harm_status validate(const harm_scene_desc *d)
+{
     if (!(d->f0_hz > 0 && std::isfinite(d->f0_hz)) || !(d->fs_hz > 0 && std::isfinite(d->fs_hz)) ||
         !(d->prf_hz > 0 && std::isfinite(d->prf_hz)))
         return fail(HARM_E_INVALID, "f0, fs and prf must be positive and finite");
@@ -216,6 +260,28 @@ harm_status validate(const harm_scene_desc *d)
         if (!(v > 0) || norm3(cross) < 1e-9 * v * p)
             return fail(HARM_E_INVALID, "antenna %d: velocity must be nonzero and not along the line of sight", i);
     }
+    // version-2 variants
+    if (!(d->speckle_tau_s >= 0 && std::isfinite(d->speckle_tau_s)))
+        return fail(HARM_E_INVALID, "speckle_tau_s must be finite and >= 0");
+    if (!std::isfinite(d->speckle_doppler_hz)) return fail(HARM_E_INVALID, "speckle_doppler_hz must be finite");
+    if (d->cwm != 0 && d->cwm != 1) return fail(HARM_E_INVALID, "cwm must be 0 or 1");
+    if (d->hetero_ncx != 0 || d->hetero_ncy != 0) {
+        if (d->hetero_ncx < 2 || d->hetero_ncy < 2 || (int64_t)d->hetero_ncx * d->hetero_ncy > 1024)
+            return fail(HARM_E_INVALID, "hetero corner grid %d x %d: need 2..1024 corners, at least 2 per axis",
+                        d->hetero_ncx, d->hetero_ncy);
+        if (!(d->hetero_tile_m > 0 && std::isfinite(d->hetero_tile_m)))
+            return fail(HARM_E_INVALID, "hetero_tile_m must be positive");
+        if (!d->hetero_u10 || !d->hetero_wind_dir_rad)
+            return fail(HARM_E_INVALID, "hetero_u10 and hetero_wind_dir_rad must not be NULL");
+        const double lx = d->nx * d->facet_m, ly = d->ny * d->facet_m;
+        if ((d->hetero_ncx - 1) * d->hetero_tile_m < lx * (1.0 - 1e-12) ||
+            (d->hetero_ncy - 1) * d->hetero_tile_m < ly * (1.0 - 1e-12))
+            return fail(HARM_E_INVALID, "hetero corner grid (%d x %d corners of %g m) does not cover the patch",
+                        d->hetero_ncx, d->hetero_ncy, d->hetero_tile_m);
+        for (int i = 0; i < d->hetero_ncx * d->hetero_ncy; ++i)
+            if (!(d->hetero_u10[i] > 0 && std::isfinite(d->hetero_u10[i])) || !std::isfinite(d->hetero_wind_dir_rad[i]))
+                return fail(HARM_E_INVALID, "hetero corner %d: wind speed must be positive, direction finite", i);
+    }
     return HARM_OK;
 }
 
@@ -242,6 +308,8 @@ void free_scene(harm_scene *s)
     if (!s) return;
     cudaStreamSynchronize(s->stream);
     for (void *p : s->allocs) cudaFree(p);
+    for (void *p : s->lut_mem)
+        if (p) cudaFree(p);
     delete s;
 }
 
@@ -290,13 +358,22 @@ harm_status harm_scene_create(const harm_scene_desc *desc, void *cuda_stream, ha
 {
     if (!out) return fail(HARM_E_INVALID, "out is NULL");
     *out = nullptr;
-    harm_status st = validate(desc);
+    harm_scene_desc dn;
+    harm_status st = normalize(desc, &dn);
     if (st != HARM_OK) return st;
+    if ((st = validate(&dn)) != HARM_OK) return st;
     harm_scene *s = new (std::nothrow) harm_scene;
     if (!s) return fail(HARM_E_OOM, "host allocation failed");
-    s->desc = *desc;
-    s->rx.assign(desc->rx, desc->rx + desc->n_channels);
+    s->desc = dn;
+    s->rx.assign(dn.rx, dn.rx + dn.n_channels);
     s->desc.rx = nullptr;
+    if (dn.hetero_ncx > 0) {
+        const int nco = dn.hetero_ncx * dn.hetero_ncy;
+        s->het_u10.assign(dn.hetero_u10, dn.hetero_u10 + nco);
+        s->het_dir.assign(dn.hetero_wind_dir_rad, dn.hetero_wind_dir_rad + nco);
+    }
+    s->desc.hetero_u10 = nullptr;
+    s->desc.hetero_wind_dir_rad = nullptr;
     s->stream = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e != cudaSuccess) {
@@ -360,6 +437,68 @@ harm_status harm_scene_set_cells(harm_scene *s, int32_t ncx, int32_t ncy, double
     s->dev.cell = cell_m;
     s->dev.cell_sigma0 = sigma0_dev;
     s->dev.cell_uv = uv_dev;
+    return HARM_OK;
+}
+
+harm_status harm_scene_set_pattern(harm_scene *s, int32_t antenna, int32_t nu, int32_t nv, double u0, double du,
+                                   double v0, double dv, const double *gain_host)
+{
+    if (!s) return fail(HARM_E_INVALID, "scene is NULL");
+    if (antenna < -1 || antenna >= s->desc.n_channels)
+        return fail(HARM_E_INVALID, "antenna %d: -1 (transmitter) or 0..%d", antenna, s->desc.n_channels - 1);
+    harm_status st = check_device(s);
+    if (st != HARM_OK) return st;
+    const int slot = antenna + 1;
+    if (gain_host) {
+        if (nu < 2 || nv < 2 || nu > 65536 || nv > 65536)
+            return fail(HARM_E_INVALID, "u-v grid %d x %d: need 2..65536 nodes per axis", nu, nv);
+        if (!(du > 0) || !(dv > 0) || !std::isfinite(du) || !std::isfinite(dv) || !std::isfinite(u0) ||
+            !std::isfinite(v0))
+            return fail(HARM_E_INVALID, "u-v grid origin must be finite and steps positive");
+        const size_t nn = (size_t)nu * nv;
+        for (size_t i = 0; i < 2 * nn; ++i)
+            if (!std::isfinite(gain_host[i])) return fail(HARM_E_INVALID, "u-v grid holds a non-finite gain");
+    }
+    HARM_CUDA(cudaStreamSynchronize(s->stream), "cudaStreamSynchronize");  // kernels may still read the old grid
+    if (s->lut_mem[slot]) {
+        cudaFree(s->lut_mem[slot]);
+        s->lut_mem[slot] = nullptr;
+    }
+    s->dev.lut_mask &= ~(1u << slot);
+    harm::PatLut L{};
+    if (gain_host) {
+        const size_t nn = (size_t)nu * nv;
+        L.nu = nu;
+        L.nv = nv;
+        L.u0 = u0;
+        L.inv_du = 1.0 / du;
+        L.v0 = v0;
+        L.inv_dv = 1.0 / dv;
+        void *p = nullptr;
+        if (s->desc.precision == HARM_PREC_FP64) {
+            HARM_CUDA(cudaMalloc(&p, nn * sizeof(double2)), "cudaMalloc u-v grid");
+            cudaError_t e = cudaMemcpy(p, gain_host, nn * sizeof(double2), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(p);
+                return cuda_fail(e, "upload u-v grid");
+            }
+            L.g64 = (const double2 *)p;
+        } else {
+            std::vector<float2> g32(nn);
+            for (size_t i = 0; i < nn; ++i) g32[i] = make_float2((float)gain_host[2 * i], (float)gain_host[2 * i + 1]);
+            HARM_CUDA(cudaMalloc(&p, nn * sizeof(float2)), "cudaMalloc u-v grid");
+            cudaError_t e = cudaMemcpy(p, g32.data(), nn * sizeof(float2), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(p);
+                return cuda_fail(e, "upload u-v grid");
+            }
+            L.g32 = (const float2 *)p;
+        }
+        s->lut_mem[slot] = p;
+        s->dev.lut_mask |= 1u << slot;
+    }
+    s->luts[slot] = L;
+    HARM_CUDA(cudaMemcpy(s->luts_dev + slot, &L, sizeof(L), cudaMemcpyHostToDevice), "upload u-v grid descriptor");
     return HARM_OK;
 }
 
@@ -461,6 +600,29 @@ harm_status build_scene_tables(harm_scene *s)
     v.cur_u = d.current_u;
     v.cur_v = d.current_v;
     v.speckle_seed = d.speckle_seed;
+    // AR(1) speckle (Eq. 10) between epochs of epoch_pulses / prf; when a pulse
+    // window starts mid-burst the recurrence is restarted from the last terms
+    // whose weight beta^m is above 2^-40
+    v.spk_beta = 0.0;
+    v.spk_q = 1.0;
+    v.spk_terms = 1;
+    if (d.speckle_tau_s > 0.0 && d.epoch_pulses > 0) {
+        double b = std::exp(-((double)d.epoch_pulses / d.prf_hz) / d.speckle_tau_s);
+        if (b > 0.0) {
+            v.spk_beta = b;
+            v.spk_q = std::sqrt(1.0 - b * b);
+            double m = std::ceil(40.0 * std::log(2.0) / -std::log(b)) + 1.0;
+            v.spk_terms = m > 1e9 ? 1000000000 : (int)m;
+        }
+    }
+    v.fd_hz = d.speckle_doppler_hz;
+    v.cwm = d.cwm;
+    v.het_ncx = d.hetero_ncx;
+    v.het_ncy = d.hetero_ncy;
+    v.het_l = d.hetero_tile_m;
+    v.het_x0 = -0.5 * nx * d.facet_m;
+    v.het_y0 = -0.5 * ny * d.facet_m;
+    v.lut_mask = 0u;
     // Kaiser window I0(beta sqrt(v)) / I0(beta) as a power series in v = 1 - (x/4)^2:
     // coefficient k is (beta^2/4)^k / (k!)^2, divided by I0(beta) = sum of them.
     {
@@ -501,31 +663,44 @@ harm_status build_scene_tables(harm_scene *s)
         }
 
     // waves: separable phasor tables e^{i kx x}, a e^{i phi} e^{i ky y}, e^{-i omega t_s}
-    std::vector<Wave> waves = wave_grid(d);
-    int nw = (int)waves.size();
+    // for every wave set
+    const WaveSets W = wave_sets(s);
+    const int nw = W.nw, nsets = W.n_sets;
     s->nw = nw;
     v.nw = nw;
-    std::vector<double> kx(nw), ky(nw), om(nw);
-    std::vector<double2> ex((size_t)nw * nx), ey((size_t)nw * ny), tt((size_t)nw * np);
-    for (int m = 0; m < nw; ++m) {
-        kx[m] = waves[m].kx;
-        ky[m] = waves[m].ky;
-        om[m] = waves[m].om;
-        for (int ix = 0; ix < nx; ++ix) {
-            double x = (ix + 0.5 - 0.5 * nx) * d.facet_m;
-            double a = waves[m].kx * x;
-            ex[(size_t)m * nx + ix] = make_double2(std::cos(a), std::sin(a));
-        }
-        for (int iy = 0; iy < ny; ++iy) {
-            double y = (iy + 0.5 - 0.5 * ny) * d.facet_m;
-            double a = waves[m].ky * y + waves[m].ph;
-            ey[(size_t)m * ny + iy] = make_double2(waves[m].amp * std::cos(a), waves[m].amp * std::sin(a));
-        }
-        for (int n = 0; n < np; ++n) {
-            double a = -waves[m].om * ps[n].ts;
-            tt[(size_t)m * np + n] = make_double2(std::cos(a), std::sin(a));
-        }
+    v.n_sets = nsets;
+    std::vector<double> kx((size_t)nsets * nw), ky((size_t)nsets * nw), om((size_t)nsets * nw),
+        kn((size_t)nsets * nw);
+    std::vector<double2> ex, ey, tt;
+    if (d.precision == HARM_PREC_FP64) {
+        ex.resize((size_t)nsets * nw * nx);
+        ey.resize((size_t)nsets * nw * ny);
+        tt.resize((size_t)nsets * nw * np);
     }
+    for (int q = 0; q < nsets; ++q)
+        for (int m = 0; m < nw; ++m) {
+            const Wave &w = W.at(q, m);
+            const size_t qm = (size_t)q * nw + m;
+            kx[qm] = w.kx;
+            ky[qm] = w.ky;
+            om[qm] = w.om;
+            kn[qm] = std::sqrt(w.kx * w.kx + w.ky * w.ky);
+            if (d.precision != HARM_PREC_FP64) continue;
+            for (int ix = 0; ix < nx; ++ix) {
+                double x = (ix + 0.5 - 0.5 * nx) * d.facet_m;
+                double a = w.kx * x;
+                ex[qm * nx + ix] = make_double2(std::cos(a), std::sin(a));
+            }
+            for (int iy = 0; iy < ny; ++iy) {
+                double y = (iy + 0.5 - 0.5 * ny) * d.facet_m;
+                double a = w.ky * y + w.ph;
+                ey[qm * ny + iy] = make_double2(w.amp * std::cos(a), w.amp * std::sin(a));
+            }
+            for (int n = 0; n < np; ++n) {
+                double a = -w.om * ps[n].ts;
+                tt[qm * np + n] = make_double2(std::cos(a), std::sin(a));
+            }
+        }
 
     harm_status st;
     if ((st = upload(s, ps, &v.pulses)) != HARM_OK) return st;
@@ -533,6 +708,16 @@ harm_status build_scene_tables(harm_scene *s)
     if ((st = upload(s, kx, &v.kx)) != HARM_OK) return st;
     if ((st = upload(s, ky, &v.ky)) != HARM_OK) return st;
     if ((st = upload(s, om, &v.om)) != HARM_OK) return st;
+    if ((st = upload(s, kn, &v.kn)) != HARM_OK) return st;
+    // u-v gain grids: none until harm_scene_set_pattern
+    s->luts.assign(1 + nc, PatLut{});
+    s->lut_mem.assign(1 + nc, nullptr);
+    {
+        const PatLut *lp = nullptr;
+        if ((st = upload(s, s->luts, &lp)) != HARM_OK) return st;
+        s->luts_dev = const_cast<PatLut *>(lp);
+        v.luts = lp;
+    }
     if (d.precision == HARM_PREC_FP64) {
         if ((st = upload(s, ex, &v.ex)) != HARM_OK) return st;
         if ((st = upload(s, ey, &v.ey)) != HARM_OK) return st;
@@ -543,7 +728,7 @@ harm_status build_scene_tables(harm_scene *s)
     if ((st = upload(s, flags, &fl)) != HARM_OK) return st;
     v.flags = const_cast<unsigned int *>(fl);
     if (d.precision == HARM_PREC_MIXED) {
-        st = build_mixed_tables(s, ps, waves);
+        st = build_mixed_tables(s, ps, W);
         if (st != HARM_OK) return fail(st, "mixed-precision table upload failed");
     }
     HARM_CUDA(cudaStreamSynchronize(s->stream), "scene upload");

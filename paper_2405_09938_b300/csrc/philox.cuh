@@ -4,7 +4,8 @@
 //
 // Streams: counter (id, 0, word2, 0) with key (seed_lo, seed_hi ^ stream).
 //   speckle   : id = facet, word2 = coherence epoch, stream 0
-//   wave phase: id = component, word2 = 0, stream 0x57415645
+//   wave phase: id = component, word2 = 0 (homogeneous sea state) or 1 + corner
+//               index (tile of a heterogeneous sea state), stream 0x57415645
 #pragma once
 #include <cstdint>
 

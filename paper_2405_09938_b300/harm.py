@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libharm.so")
 
-HARM_ABI_VERSION = 1
+HARM_ABI_VERSION = 2
 HARM_MAX_CHANNELS = 16
 HARM_OK, HARM_E_INVALID, HARM_E_CUDA, HARM_E_OOM, HARM_E_TIMEOUT, HARM_E_UNSUPPORTED = range(6)
 HARM_C64, HARM_C128 = 0, 1
@@ -57,6 +57,12 @@ class harm_scene_desc(C.Structure):
         ("taps", C.c_int32),
         ("kaiser_beta", C.c_double),
         ("precision", C.c_int32),
+        # abi_version >= 2
+        ("speckle_tau_s", C.c_double), ("speckle_doppler_hz", C.c_double),
+        ("cwm", C.c_int32),
+        ("hetero_ncx", C.c_int32), ("hetero_ncy", C.c_int32),
+        ("hetero_tile_m", C.c_double),
+        ("hetero_u10", C.POINTER(C.c_double)), ("hetero_wind_dir_rad", C.POINTER(C.c_double)),
     ]
 
 
@@ -74,6 +80,8 @@ SIGNATURES = {
     "harm_scene_destroy": (C.c_int, [_VP]),
     "harm_scene_query": (C.c_int, [_VP, C.POINTER(harm_scene_info)]),
     "harm_scene_set_cells": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_double, _VP, _VP]),
+    "harm_scene_set_pattern": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
+                                         C.c_double, C.c_double, C.POINTER(C.c_double)]),
     "harm_facets_generate": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP]),
     "harm_echo_accumulate": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP, C.c_int, C.c_int32]),
     "harm_echo_adjoint": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP, C.c_int, _VP, _VP]),
@@ -126,8 +134,10 @@ def _antenna(a):
 
 def make_desc(d: dict, precision: int):
     """Marshal a scene dictionary (see :mod:`harm_scenes`) into harm_scene_desc.
-    Returns (desc, keepalive) -- the rx array must outlive the create call."""
+    Returns (desc, keepalive) -- the arrays it points to must outlive the create
+    call."""
     rx = (harm_antenna * len(d["rx"]))(*[_antenna(a) for a in d["rx"]])
+    keep = [rx]
     s = harm_scene_desc()
     s.abi_version = HARM_ABI_VERSION
     s.struct_size = C.sizeof(harm_scene_desc)
@@ -146,7 +156,19 @@ def make_desc(d: dict, precision: int):
     s.static_surface = d["static_surface"]
     s.taps, s.kaiser_beta = d["taps"], d["kaiser_beta"]
     s.precision = precision
-    return s, rx
+    s.speckle_tau_s = d.get("speckle_tau_s", 0.0)
+    s.speckle_doppler_hz = d.get("speckle_doppler_hz", 0.0)
+    s.cwm = int(d.get("cwm", 0))
+    het = d.get("hetero")
+    if het is not None:
+        u = np.ascontiguousarray(het["u10"], dtype=np.float64)
+        w = np.ascontiguousarray(het["wind_dir"], dtype=np.float64)
+        s.hetero_ncy, s.hetero_ncx = u.shape
+        s.hetero_tile_m = het["tile_m"]
+        s.hetero_u10 = u.ctypes.data_as(C.POINTER(C.c_double))
+        s.hetero_wind_dir_rad = w.ctypes.data_as(C.POINTER(C.c_double))
+        keep += [u, w]
+    return s, keep
 
 
 def _stream_handle(stream):
@@ -198,7 +220,29 @@ def harm_scene_create(desc: dict, precision: int = HARM_PREC_FP64, stream=None) 
     out = C.c_void_p()
     _check(lib.harm_scene_create(C.byref(s), C.c_void_p(_stream_handle(stream)), C.byref(out)))
     del keep
-    return Scene(out, desc, precision, stream)
+    scene = Scene(out, desc, precision, stream)
+    # u-v gain grids listed in the descriptor dictionary ("tx" or channel index)
+    for ant, pat in (desc.get("patterns") or {}).items():
+        harm_scene_set_pattern(scene, -1 if ant == "tx" else int(ant), pat)
+    return scene
+
+
+def harm_scene_set_pattern(scene: Scene, antenna: int, pattern):
+    """Set (pattern = dict with u0, du, v0, dv and a complex [nv, nu] "gain"
+    array) or remove (pattern = None) the u-v gain grid of an antenna (-1 =
+    transmitter, c = receive channel c)."""
+    lib = load_library()
+    if pattern is None:
+        _check(lib.harm_scene_set_pattern(scene.handle, antenna, 0, 0, 0.0, 0.0, 0.0, 0.0, None))
+        return
+    g = np.asarray(pattern["gain"], dtype=np.complex128)
+    if g.ndim != 2:
+        raise HarmError(HARM_E_INVALID, "gain must be a 2-D [nv, nu] array")
+    buf = np.ascontiguousarray(np.stack([g.real, g.imag], axis=-1))
+    nv, nu = g.shape
+    _check(lib.harm_scene_set_pattern(scene.handle, antenna, nu, nv, pattern["u0"], pattern["du"],
+                                      pattern["v0"], pattern["dv"],
+                                      buf.ctypes.data_as(C.POINTER(C.c_double))))
 
 
 def harm_scene_destroy(scene: Scene):

@@ -92,3 +92,40 @@ def test_invalid_descriptor_rejected_without_device_work():
     assert lib.harm_echo_accumulate(None, 0, 1, None, 0, 1) == harm.HARM_E_INVALID
     assert lib.harm_scene_sync(None) == harm.HARM_E_INVALID
     assert lib.harm_scene_destroy(None) == harm.HARM_OK
+
+
+def test_version_1_descriptor_and_variant_validation():
+    """A version-1 descriptor (the prefix before the variant fields) passes
+    validation; bad variant fields are rejected, all before any CUDA call."""
+    import harm_scenes as hs
+    lib = harm.load_library(harm_build.build())
+    d = hs.small_static()
+    out = ctypes.c_void_p()
+    s, keep = harm.make_desc(d, harm.HARM_PREC_FP64)
+    s.abi_version = 1
+    s.struct_size = harm.harm_scene_desc.speckle_tau_s.offset
+    st = lib.harm_scene_create(ctypes.byref(s), None, ctypes.byref(out))
+    assert st != harm.HARM_E_INVALID, lib.harm_last_error()
+    s.struct_size = ctypes.sizeof(harm.harm_scene_desc)  # a version-1 caller cannot send the longer struct
+    assert lib.harm_scene_create(ctypes.byref(s), None, ctypes.byref(out)) == harm.HARM_E_INVALID
+    s, keep = harm.make_desc(d, harm.HARM_PREC_FP64)
+    s.abi_version = 3
+    assert lib.harm_scene_create(ctypes.byref(s), None, ctypes.byref(out)) == harm.HARM_E_INVALID
+    for field, value in [("speckle_tau_s", -1.0), ("cwm", 2), ("speckle_doppler_hz", float("nan"))]:
+        s, keep = harm.make_desc(d, harm.HARM_PREC_FP64)
+        setattr(s, field, value)
+        assert lib.harm_scene_create(ctypes.byref(s), None, ctypes.byref(out)) == harm.HARM_E_INVALID, field
+    # a corner grid that does not cover the patch (200 m patch, 2 x 2 corners of 150 m)
+    dh = hs.hetero_sea(d, tile_m=150.0)
+    dh["hetero"]["u10"] = dh["hetero"]["u10"][:2, :2]
+    dh["hetero"]["wind_dir"] = dh["hetero"]["wind_dir"][:2, :2]
+    s, keep = harm.make_desc(dh, harm.HARM_PREC_FP64)
+    assert lib.harm_scene_create(ctypes.byref(s), None, ctypes.byref(out)) == harm.HARM_E_INVALID
+    assert b"cover" in lib.harm_last_error()
+    dh = hs.hetero_sea(d, tile_m=100.0)
+    dh["hetero"]["u10"][0, 0] = 0.0
+    s, keep = harm.make_desc(dh, harm.HARM_PREC_FP64)
+    assert lib.harm_scene_create(ctypes.byref(s), None, ctypes.byref(out)) == harm.HARM_E_INVALID
+    assert out.value is None
+    # pattern setter on a NULL scene
+    assert lib.harm_scene_set_pattern(None, -1, 2, 2, 0.0, 1.0, 0.0, 1.0, None) == harm.HARM_E_INVALID
