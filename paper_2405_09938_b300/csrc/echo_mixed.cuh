@@ -135,8 +135,14 @@ struct MixedArgs {
 // the constant bank.
 // Each coefficient is stored as the pair (c, c) so that the packed two-facet
 // evaluation reads it as one 64-bit constant operand; scalar code reads .x.
+// The Kaiser-sinc taps are symmetric, h_(7-j)(t) = h_j(-t) for t = 2f - 1 (the
+// window is even), so taps j and 7 - j come from the even and odd parts of one
+// polynomial: h_j = E_j(t^2) + t O_j(t^2), h_(7-j) = E_j(t^2) - t O_j(t^2), j = 0..3.
+constexpr int kTapEven = kTapDeg / 2 + 1;        // coefficients of E_j in t^2
+constexpr int kTapOdd = (kTapDeg + 1) / 2;       // coefficients of O_j in t^2
 struct PolyArgs {
-    float2 tap[8][kTapDeg + 1];
+    float2 tap_e[4][kTapEven];
+    float2 tap_o[4][kTapOdd];
     float2 sinc2[kSincDeg + 1];
 };
 
@@ -896,13 +902,20 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
             kba = Q.kbase + (int)kf.x - 3;
             kbb = Q.kbase + (int)kf.y - 3;
             const float2 t = fma2(dup(2.0f), fr, dup(-1.0f));
+            const float2 t2 = mul2(t, t);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                float2 v = P.tap[j][kTapDeg];
+            for (int j = 0; j < 4; ++j) {
+                float2 ev = P.tap_e[j][kTapEven - 1];
 #pragma unroll
-                for (int d = kTapDeg - 1; d >= 0; --d) v = fma2(v, t, P.tap[j][d]);
-                ha[j] = v.x;
-                hb[j] = v.y;
+                for (int d = kTapEven - 2; d >= 0; --d) ev = fma2(ev, t2, P.tap_e[j][d]);
+                float2 od = P.tap_o[j][kTapOdd - 1];
+#pragma unroll
+                for (int d = kTapOdd - 2; d >= 0; --d) od = fma2(od, t2, P.tap_o[j][d]);
+                const float2 lo = fma2(od, t, ev), hi = fma2(neg2(od), t, ev);
+                ha[j] = lo.x;
+                hb[j] = lo.y;
+                ha[7 - j] = hi.x;
+                hb[7 - j] = hi.y;
             }
         }
         sink.put2(A, ch, Q.kbase, kba, kbb, ha, hb, vre, vim, qx, qy, PR.k0t, G.va, G.vb);
@@ -1384,8 +1397,17 @@ MixedArgs make_args(const DevScene &S, const MixedTables &M)
 PolyArgs make_poly(const MixedTables &M)
 {
     PolyArgs P;
-    for (int j = 0; j < 8; ++j)
-        for (int d = 0; d <= kTapDeg; ++d) P.tap[j][d] = make_float2(M.tap[j][d], M.tap[j][d]);
+    // even / odd parts of taps j and 7 - j, averaged so that the symmetry is exact
+    for (int j = 0; j < 4; ++j) {
+        for (int k = 0; k < kTapEven; ++k) {
+            const float c = 0.5f * (M.tap[j][2 * k] + M.tap[7 - j][2 * k]);
+            P.tap_e[j][k] = make_float2(c, c);
+        }
+        for (int k = 0; k < kTapOdd; ++k) {
+            const float c = 0.5f * (M.tap[j][2 * k + 1] - M.tap[7 - j][2 * k + 1]);
+            P.tap_o[j][k] = make_float2(c, c);
+        }
+    }
     for (int d = 0; d <= kSincDeg; ++d) P.sinc2[d] = make_float2(M.sinc2[d], M.sinc2[d]);
     return P;
 }
