@@ -14,13 +14,14 @@
 //        r - R = a + (b - a^2) / (2R) + (a^3 - a b) / (2R^2),  a = u.xi, b = |xi|^2
 //     for the facet offset xi from the reference point; the linear phase term
 //     K0 (u_t + u_r).xi is split into exactly-reduced lattice steps.
-//  3. For each pulse: each thread evaluates its two facets (rows w and w + 8 of
-//     the tile) together in packed FP32x2 arithmetic: Horner in time, then per
-//     channel the contribution (Eq. 3, 4, 16) and its 8 Kaiser-sinc taps
-//     (polynomials in the fractional bin). The warp pre-reduces its 32 lanes'
-//     taps: each lane writes its taps into its own (row-rotated) column of a
-//     per-warp [16 bin x 32 lane] shared buffer at the rows of its bins, then each
-//     lane sums one bin-row half with vector loads; one shared atomic per
+//  3. For each pulse: each thread evaluates its two facets (adjacent rows 2w and
+//     2w + 1 of the tile) together in packed FP32x2 arithmetic: Horner in time,
+//     then per channel the contribution (Eq. 3, 4, 16) and its 8 Kaiser-sinc taps
+//     (polynomials in the fractional bin). The two facets' first bins differ by at
+//     most one, so each lane merges their taps into 9 values; the warp pre-reduces
+//     its 32 lanes: each lane writes its values into its own (row-rotated) column
+//     of a per-warp [16 bin x 32 lane] shared buffer at the rows of its bins, then
+//     each lane sums one bin-row half with vector loads; one shared atomic per
 //     (bin, component) adds the warp's window to the CTA range tile, which is
 //     flushed to the IQ with one vector atomic per bin and channel.
 //  The adjoint runs the same per-pulse arithmetic and gathers the residual
@@ -626,6 +627,90 @@ __device__ __forceinline__ void warp_scatter(float *buf, float2 *tile_c, int til
     }
 }
 
+// Warp pre-reduction of both facets of every lane in one pass. The facets sit
+// in adjacent rows, so facet b's taps start at most one bin away from facet a's:
+// each lane combines them into 9 complex values at bins k0 .. k0 + 8 (k0 the lower
+// of the two first bins) and writes those into its rotated column as above. The
+// pass needs every lane's first bins within one of each other and all lanes' k0
+// within 7 bins; otherwise it returns false and the caller reduces the facets one
+// at a time.
+template <typename OutT>
+__device__ __forceinline__ bool warp_scatter_pair(float *buf, float2 *tile_c, int tile_base, int kba, int kbb,
+                                                  bool va, bool vb, const float ha[8], const float hb[8], float2 vre,
+                                                  float2 vim, int nr, OutT *grow, unsigned int *flags)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    // a masked facet contributes nothing and takes the other facet's bins
+    float sra = vre.x, sia = vim.x, srb = vre.y, sib = vim.y;
+    if (!va) {
+        sra = sia = 0.0f;
+        kba = kbb;
+    }
+    if (!vb) {
+        srb = sib = 0.0f;
+        kbb = kba;
+    }
+    const bool valid = va || vb;
+    const int k0 = min(kba, kbb);
+    const int kmin = __reduce_min_sync(FULL, valid ? k0 : INT_MAX);
+    if (kmin == INT_MAX) return true;
+    const int kmax = __reduce_max_sync(FULL, valid ? k0 : INT_MIN);
+    if (kmax - kmin > SBINS - 9 || __any_sync(FULL, valid && abs(kbb - kba) > 1)) return false;
+    const int o = k0 - kmin;
+    const int ll = lane & 15;
+    const int hbase = lane < 16 ? 0 : SHALF;
+    const int rot = (ll - 4 * o) & 15;
+    float *col[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) col[m] = buf + hbase + 2 * ((rot - 4 * m) & 15) + o * SROW;
+    if (valid) {
+        const bool sa = kba != k0, sb = kbb != k0;  // the facet starts one bin above k0
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const float a = sa ? (j > 0 ? ha[j - 1] : 0.0f) : (j < 8 ? ha[j] : 0.0f);
+            const float b = sb ? (j > 0 ? hb[j - 1] : 0.0f) : (j < 8 ? hb[j] : 0.0f);
+            *reinterpret_cast<float2 *>(col[j & 3] + j * SROW) =
+                make_float2(fmaf(b, srb, a * sra), fmaf(b, sib, a * sia));
+        }
+    }
+    __syncwarp();
+    const int w = lane >> 1, half = lane & 1;
+    float ar = 0.0f, ai = 0.0f;
+    if (w < kmax - kmin + 9) {
+        const float4 *rp = reinterpret_cast<const float4 *>(buf + w * SROW + half * SHALF);
+        float4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = rp[q];
+        float2 c[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) c[q] = add2(make_float2(v[q].x, v[q].y), make_float2(v[q].z, v[q].w));
+        const float2 sum =
+            add2(add2(add2(c[0], c[1]), add2(c[2], c[3])), add2(add2(c[4], c[5]), add2(c[6], c[7])));
+        ar = sum.x;
+        ai = sum.y;
+    }
+    ar += __shfl_xor_sync(FULL, ar, 1);
+    ai += __shfl_xor_sync(FULL, ai, 1);
+    __syncwarp();
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < 9; ++j) *reinterpret_cast<float2 *>(col[j & 3] + j * SROW) = make_float2(0.f, 0.f);
+    }
+    const float val = half ? ai : ar;
+    const int k = kmin + w;
+    if (val != 0.0f && k >= 0 && k < nr) {
+        const int tw = k - tile_base;
+        if (tw >= 0 && tw < WT) {
+            atomicAdd(reinterpret_cast<float *>(tile_c + tw) + half, val);
+        } else {
+            gadd1<OutT>(grow, (size_t)k, half, val);
+            atomicAdd(flags + 2, 1u);
+        }
+    }
+    return true;
+}
+
 struct FacetGeo {
     float xi_y;          // y offset from the tile reference point (exact)
     float fj;            // row offset index
@@ -654,6 +739,9 @@ struct ScatterSink {
         float2 *tile_c = tiles + (buf * A.S.nc + ch) * WT;
         const int tile_base = kbase - WT_LO;
         OutT *grow = iq + 2 * ((size_t)ch * np + (n - n0)) * A.S.nr;
+        if (warp_scatter_pair<OutT>(stage, tile_c, tile_base, kba, kbb, va, vb, ha, hb, vre, vim, A.S.nr, grow,
+                                    A.S.flags))
+            return;
         warp_scatter<OutT>(stage, tile_c, tile_base, kba, va, ha, vre.x, vim.x, A.S.nr, grow, A.S.flags);
         warp_scatter<OutT>(stage, tile_c, tile_base, kbb, vb, hb, vre.y, vim.y, A.S.nr, grow, A.S.flags);
     }
@@ -1037,10 +1125,14 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
     const float fi = (float)(ix - iref);
 
     FacetGeo ga, gb;
-    facet_setup(A, ix, I.ty0 + warp, jref, ga);
-    facet_setup(A, ix, I.ty0 + warp + NWARP, jref, gb);
+    // rows of the thread's two facets: adjacent rows 2w, 2w + 1 (16-row tiles; their
+    // range bins differ by at most one, so the warp reduces both in one pass), or
+    // row w alone (8-row tiles)
+    const int iya = I.ty0 + (two ? 2 * warp : warp), iyb = iya + 1;
+    facet_setup(A, ix, iya, jref, ga);
+    facet_setup(A, ix, iyb, jref, gb);
     float ca[NF][kOrders], cb[NF][kOrders];
-    item_coeffs<NF>(sm, A, I.batch, I.tx0, I.ty0, I.ty, ix, I.ty0 + warp, I.ty0 + warp + NWARP, two, ca, cb);
+    item_coeffs<NF>(sm, A, I.batch, I.tx0, I.ty0, I.ty, ix, iya, iyb, two, ca, cb);
     __syncthreads();
     // the warp buffers share memory with the wave-table chunk: clear them
     for (int i = threadIdx.x; i < NWARP * SBINS * SROW; i += NT) sm.stage[i] = 0.0f;
@@ -1258,10 +1350,11 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     const float fi = (float)(ix - iref);
 
     FacetGeo ga, gb;
-    facet_setup(A, ix, ty0 + warp, jref, ga);
-    facet_setup(A, ix, ty0 + warp + NWARP, jref, gb);
+    const int iya = ty0 + 2 * warp, iyb = iya + 1;  // the forward path's facet rows
+    facet_setup(A, ix, iya, jref, ga);
+    facet_setup(A, ix, iyb, jref, gb);
     float ca[NF][kOrders], cb[NF][kOrders];
-    item_coeffs<NF>(sm, A, batch, tx0, ty0, TY, ix, ty0 + warp, ty0 + warp + NWARP, true, ca, cb);
+    item_coeffs<NF>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, true, ca, cb);
     if (Var<V>::LUT) {
         __syncthreads();
         stage_luts(sm, S);
@@ -1348,7 +1441,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     if (pa >= pe) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ix = tx0 + lane;
-    const int iya = ty0 + warp, iyb = ty0 + warp + NWARP;
+    const int iya = ty0 + 2 * warp, iyb = iya + 1;
     const bool va = ix < S.nx && iya < S.ny, vb = ix < S.nx && iyb < S.ny;
     float ca[NF][kOrders], cb[NF][kOrders];
     item_coeffs<NF>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, true, ca, cb);
