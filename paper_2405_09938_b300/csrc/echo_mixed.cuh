@@ -907,6 +907,7 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
 
     const AntRec2 *RX = sm.rx2 + pi * nc;
     const ChanRec2 *CH = sm.ch2 + pi * nc;
+    float2 gr_prev = make_float2(0.0f, 0.0f);
     for (int ch = 0; ch < nc; ++ch) {
         const AntRec2 R = RX[ch];
         const ChanRec2 Q = CH[ch];
@@ -916,13 +917,20 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
         const float2 dr = add2(ar, qr);
         const float2 er = mul2(dr, R.invR);
         const float2 rho_r = fma2(er, er, sub2(one, er));
-        const float2 ur = mul2(add2(R.u0, fma2(X0, R.aRx, fma2(X1, R.aRy, mul2(eta, R.aRz)))), rho_r);
-        const float2 vr = mul2(add2(R.v0, fma2(X0, R.eRx, fma2(X1, R.eRy, mul2(eta, R.eRz)))), rho_r);
         float2 gr, gri;
-        if constexpr (LUT)
+        if constexpr (LUT) {
+            const float2 ur = mul2(add2(R.u0, fma2(X0, R.aRx, fma2(X1, R.aRy, mul2(eta, R.aRz)))), rho_r);
+            const float2 vr = mul2(add2(R.v0, fma2(X0, R.eRx, fma2(X1, R.eRy, mul2(eta, R.eRz)))), rho_r);
             pair_gain(sm, S, P, 1 + ch, A.rx_laz_l[ch], A.rx_lel_l[ch], ur, vr, gr, gri);
-        else
+        } else if ((S.rx_share >> ch) & 1u) {
+            // phase centre of the same receive antenna as channel ch - 1: same gain
+            gr = gr_prev;
+        } else {
+            const float2 ur = mul2(add2(R.u0, fma2(X0, R.aRx, fma2(X1, R.aRy, mul2(eta, R.aRz)))), rho_r);
+            const float2 vr = mul2(add2(R.v0, fma2(X0, R.eRx, fma2(X1, R.eRy, mul2(eta, R.eRz)))), rho_r);
             gr = mul2(sinc2_2(P, mul2(dup(A.rx_laz_l[ch]), ur)), sinc2_2(P, mul2(dup(A.rx_lel_l[ch]), vr)));
+        }
+        gr_prev = gr;
         const float2 qx = neg2(fma2(fma2(X0, R.invR, R.ux), rho_r, rt0));
         const float2 qy = neg2(fma2(fma2(X1, R.invR, R.uy), rho_r, rt1));
         const float2 qz = neg2(fma2(fma2(eta, R.invR, R.uz), rho_r, rt2));

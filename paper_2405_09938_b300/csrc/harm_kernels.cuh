@@ -11,7 +11,7 @@ namespace harm {
 
 // Mixed-precision path tables (FP32 separable waves and the Taylor-in-time
 // tables of each pulse batch, plus the tap polynomials).
-constexpr int kTapDeg = 8;      // degree of each tap polynomial in t = 2f - 1 (fit error 1.8e-7)
+constexpr int kTapDeg = 7;      // degree of each tap polynomial in t = 2f - 1 (fit error 9e-7)
 constexpr int kSincDeg = 7;     // degree of the sinc^2 polynomial in t = 2x^2 - 1, |x| <= 1
 constexpr int kOrders = 6;      // Taylor orders in time: tau^0 .. tau^5
 

@@ -616,6 +616,18 @@ harm_status build_scene_tables(harm_scene *s)
         }
     }
     v.fd_hz = d.speckle_doppler_hz;
+    // phase centres of one receive antenna: same aperture, same velocity, within
+    // 50 m of the previous channel. Their direction cosines to any facet differ by
+    // ~(patch size / R) x (separation / R) ~ 1e-8, so the mixed path evaluates the
+    // analytic pattern once per antenna.
+    v.rx_share = 0u;
+    for (int c = 1; c < nc; ++c) {
+        const harm_antenna &a = s->rx[c], &b = s->rx[c - 1];
+        double sep[3] = {a.pos0[0] - b.pos0[0], a.pos0[1] - b.pos0[1], a.pos0[2] - b.pos0[2]};
+        if (a.len_az == b.len_az && a.len_el == b.len_el && a.vel[0] == b.vel[0] && a.vel[1] == b.vel[1] &&
+            a.vel[2] == b.vel[2] && norm3(sep) <= 50.0)
+            v.rx_share |= 1u << c;
+    }
     v.cwm = d.cwm;
     v.het_ncx = d.hetero_ncx;
     v.het_ncy = d.hetero_ncy;
