@@ -52,7 +52,7 @@ constexpr int NT = 256;       // threads per CTA
 constexpr int NWARP = NT / 32;
 constexpr int WT = 48;        // range bins per channel in the CTA tile
 constexpr int WT_LO = 22;     // tile window starts WT_LO bins below the reference bin
-constexpr int NBR = 32;       // pulses per chunk of FP64 tile references
+constexpr int NBR = 16;       // pulses per chunk of FP64 tile references
 constexpr int NBG = 128;      // pulses per work item (time-Taylor window of the generator)
 constexpr int WCH = 128;      // wave components per shared-memory chunk
 constexpr int SROW = 72;      // floats per bin row of the warp buffer (2 halves of 32 + pad)
@@ -149,7 +149,7 @@ struct PolyArgs {
 
 // Shared-memory layout (bytes), sized for nc channels and nf state fields.
 struct Layout {
-    int w, tile, tx, rx, ch, pr, txd, stage, lut, total;
+    int w, tile, tx, rx, ch, pr, txd, stage, lut, coef, total;
 };
 
 // The wave-table chunk (generator phase) and the warp buffers (pulse loop) are
@@ -171,6 +171,9 @@ __host__ __device__ inline Layout layout(int nc, bool dup, int nf)
     L.pr = o;    o += NBR * (int)sizeof(PulseRec);
     L.txd = o;   o += NBR * 4 * 8;
     L.lut = o;   o += (1 + kMaxCh) * (int)sizeof(PatLutF);
+    // Taylor coefficients of the thread's two facets, [3][kOrders][NT] float2, for the
+    // linear surface (the 8-field CWM keeps them in registers)
+    L.coef = o;  o += nf == 3 ? 3 * kOrders * NT * 8 : 0;
     L.total = o;
     return L;
 }
@@ -188,6 +191,7 @@ struct Smem {
     double *txd;     // [NBR][4]
     float *stage;    // [NWARP][SBINS][SROW]
     PatLutF *lut;    // [1 + nc] u-v gain grids (LUT variant)
+    float2 *coef;    // [3][kOrders][NT] Taylor coefficients (linear surface)
 };
 
 __device__ __forceinline__ Smem carve(unsigned char *raw, int nc, bool dup, int nf)
@@ -206,6 +210,7 @@ __device__ __forceinline__ Smem carve(unsigned char *raw, int nc, bool dup, int 
     s.txd = reinterpret_cast<double *>(raw + L.txd);
     s.stage = reinterpret_cast<float *>(raw + L.stage);
     s.lut = reinterpret_cast<PatLutF *>(raw + L.lut);
+    s.coef = reinterpret_cast<float2 *>(raw + L.coef);
     return s;
 }
 
@@ -842,14 +847,14 @@ __device__ __forceinline__ void pair_gain(const Smem &sm, const DevScene &S, con
 
 // Forward contribution of the thread's two facets for pulse pi (chunk index),
 // every channel, on FP32x2 pairs (facet a in .x, facet b in .y); transcendentals
-// and integer work per element. C holds the Taylor coefficients of the NF state
-// fields. V selects the variants: with the Choppy Wave Model the facets sit at
+// and integer work per element. fs holds the NF state fields of the two facets
+// at this pulse. V selects the variants: with the Choppy Wave Model the facets sit at
 // their rest positions moved by the horizontal displacement, their normal is the
 // cross product of the displaced surface's tangents and their area scales with
 // its vertical component; with u-v grids the pattern gains are complex.
 template <int TAPS, int V, typename Sink>
 __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A, const PolyArgs &P, const PairGeo &G,
-                                             const float2 C[Var<V>::NF][kOrders], int pi, float xi_x, float fi,
+                                             const float2 fs[Var<V>::NF], int pi, float xi_x, float fi,
                                              Sink &sink)
 {
     constexpr bool CWM = Var<V>::CWM, LUT = Var<V>::LUT;
@@ -857,16 +862,15 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
     const int nc = S.nc;
     const float2 one = make_float2(1.0f, 1.0f);
     const PulseRec PR = sm.pr[pi];
-    const float2 tau = dup(PR.tau);
-    const float2 eta = horner2(C[0], tau);
-    const float2 sx = horner2(C[1], tau);
-    const float2 sy = horner2(C[2], tau);
+    const float2 eta = fs[0];
+    const float2 sx = fs[1];
+    const float2 sy = fs[2];
     float2 X0 = dup(xi_x), X1 = G.xi_y;
     float2 Dx, Dy, nvx, nvy, nvz, areaf;
     if constexpr (CWM) {
-        Dx = horner2(C[3], tau);
-        Dy = horner2(C[4], tau);
-        const float2 jxx = horner2(C[5], tau), jxy = horner2(C[6], tau), jyy = horner2(C[7], tau);
+        Dx = fs[3];
+        Dy = fs[4];
+        const float2 jxx = fs[5], jxy = fs[6], jyy = fs[7];
         X0 = add2(X0, Dx);
         X1 = add2(X1, Dy);
         const float2 txx = add2(one, jxx), tyy = add2(one, jyy);
@@ -1114,6 +1118,40 @@ __device__ __forceinline__ void item_coeffs(const Smem &sm, const MixedArgs &A, 
     }
 }
 
+// Keep the item's Taylor coefficients where the pulse loop reads them: a
+// thread-private column of shared memory for the linear surface (frees 36
+// registers for the per-channel arithmetic), registers for the CWM.
+template <int NF>
+__device__ __forceinline__ void store_coeffs(const Smem &sm, const float2 C[NF][kOrders])
+{
+    if constexpr (NF == 3) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+            for (int o = 0; o < kOrders; ++o) sm.coef[(f * kOrders + o) * NT + threadIdx.x] = C[f][o];
+    }
+}
+
+// State fields of the two facets at time offset tau (Horner in time).
+template <int NF>
+__device__ __forceinline__ void eval_state(const Smem &sm, const float2 C[NF][kOrders], float tau, float2 st[NF])
+{
+    const float2 t = dup(tau);
+    if constexpr (NF == 3) {
+        const float2 *cs = sm.coef + threadIdx.x;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+            float2 r = cs[(f * kOrders + kOrders - 1) * NT];
+#pragma unroll
+            for (int o = kOrders - 2; o >= 0; --o) r = fma2(r, t, cs[(f * kOrders + o) * NT]);
+            st[f] = r;
+        }
+    } else {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) st[f] = horner2(C[f], t);
+    }
+}
+
 // One forward work item (tile x pulse batch) of one scene. Every thread of the
 // CTA calls it; it starts and ends with the CTA's range tiles all zero.
 template <int TAPS, typename OutT, int V>
@@ -1169,6 +1207,7 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
     for (int f = 0; f < NF; ++f)
 #pragma unroll
         for (int o = 0; o < kOrders; ++o) C[f][o] = make_float2(ca[f][o], two ? cb[f][o] : ca[f][o]);
+    store_coeffs<NF>(sm, C);
     for (int c0 = I.pa; c0 < I.pe; c0 += NBR) {
         const int ce = min(c0 + NBR, I.pe);
         __syncthreads();  // the previous chunk's flush is done with the records
@@ -1193,7 +1232,9 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
                 const int buf = n & 1;
                 sink.n = n;
                 sink.buf = buf;
-                facet_pulse2<TAPS, V>(sm, A, P, G, C, pi, xi_x, fi, sink);
+                float2 st[NF];
+                eval_state<NF>(sm, C, sm.pr[pi].tau, st);
+                facet_pulse2<TAPS, V>(sm, A, P, G, st, pi, xi_x, fi, sink);
                 __syncthreads();
                 for (int i = threadIdx.x; i < nc * WT; i += NT) {
                     int ch = i / WT, w = i % WT;
@@ -1381,6 +1422,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     for (int f = 0; f < NF; ++f)
 #pragma unroll
         for (int o = 0; o < kOrders; ++o) C[f][o] = make_float2(ca[f][o], cb[f][o]);
+    store_coeffs<NF>(sm, C);
     GatherSink2<InT> sink;
     sink.win = sm.tile;
     sink.resid = resid;
@@ -1422,7 +1464,9 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
                 }
                 __syncthreads();
                 sink.n = n;
-                facet_pulse2<TAPS, V>(sm, A, P, G, C, pi, xi_x, fi, sink);
+                float2 st[NF];
+                eval_state<NF>(sm, C, sm.pr[pi].tau, st);
+                facet_pulse2<TAPS, V>(sm, A, P, G, st, pi, xi_x, fi, sink);
             }
         }
     }
