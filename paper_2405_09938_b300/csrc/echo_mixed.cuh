@@ -155,6 +155,9 @@ struct Layout {
 // The wave-table chunk (generator phase) and the warp buffers (pulse loop) are
 // never live at the same time and share one region; the warp buffers are
 // cleared after the generator phase.
+// Every region starts on a 16-byte boundary (regions are read with 128-bit loads).
+__host__ __device__ inline int align16(int o) { return (o + 15) & ~15; }
+
 __host__ __device__ inline Layout layout(int nc, bool dup, int nf)
 {
     Layout L;
@@ -164,17 +167,17 @@ __host__ __device__ inline Layout layout(int nc, bool dup, int nf)
     L.w = o;
     L.stage = o;
     o += wbytes > sbytes ? wbytes : sbytes;
-    L.tile = o;  o += 2 * nc * WT * 8;
-    L.tx = o;    o += NBR * (int)(dup ? sizeof(AntRec2) : sizeof(AntRec));
-    L.rx = o;    o += NBR * nc * (int)(dup ? sizeof(AntRec2) : sizeof(AntRec));
-    L.ch = o;    o += NBR * nc * (int)(dup ? sizeof(ChanRec2) : sizeof(ChanRec));
-    L.pr = o;    o += NBR * (int)sizeof(PulseRec);
-    L.txd = o;   o += NBR * 4 * 8;
-    L.lut = o;   o += (1 + kMaxCh) * (int)sizeof(PatLutF);
+    L.tile = o = align16(o);  o += 2 * nc * WT * 8;
+    L.tx = o = align16(o);    o += NBR * (int)(dup ? sizeof(AntRec2) : sizeof(AntRec));
+    L.rx = o = align16(o);    o += NBR * nc * (int)(dup ? sizeof(AntRec2) : sizeof(AntRec));
+    L.ch = o = align16(o);    o += NBR * nc * (int)(dup ? sizeof(ChanRec2) : sizeof(ChanRec));
+    L.pr = o = align16(o);    o += NBR * (int)sizeof(PulseRec);
+    L.txd = o = align16(o);   o += NBR * 4 * 8;
+    L.lut = o = align16(o);   o += (1 + kMaxCh) * (int)sizeof(PatLutF);
     // Taylor coefficients of the thread's two facets, [3][kOrders][NT] float2, for the
     // linear surface (the 8-field CWM keeps them in registers)
-    L.coef = o;  o += nf == 3 ? 3 * kOrders * NT * 8 : 0;
-    L.total = o;
+    L.coef = o = align16(o);  o += nf == 3 ? 3 * kOrders * NT * 8 : 0;
+    L.total = align16(o);
     return L;
 }
 
@@ -704,11 +707,12 @@ __device__ __forceinline__ bool warp_scatter_pair(float *buf, float2 *tile_c, in
     }
     const float val = half ? ai : ar;
     const int k = kmin + w;
-    if (val != 0.0f && k >= 0 && k < nr) {
+    if (val != 0.0f) {
         const int tw = k - tile_base;
-        if (tw >= 0 && tw < WT) {
+        if ((unsigned)tw < (unsigned)WT) {
+            // bins outside [0, nr) are dropped when the tile is flushed
             atomicAdd(reinterpret_cast<float *>(tile_c + tw) + half, val);
-        } else {
+        } else if (k >= 0 && k < nr) {
             gadd1<OutT>(grow, (size_t)k, half, val);
             atomicAdd(flags + 2, 1u);
         }
@@ -942,7 +946,8 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
         float2 amp_s = G.amp_static;
         if (!S.static_surface) {
             const float2 qh2 = fma2(qx, qx, mul2(qy, qy));
-            const float2 rq = make_float2(qh2.x > 0.0f ? rsqrtf(qh2.x) : 0.0f, qh2.y > 0.0f ? rsqrtf(qh2.y) : 0.0f);
+            // 1 / |Q_H| (clamped: Q_H = 0 gives cos phi = 0)
+            const float2 rq = make_float2(rsqrtf(fmaxf(qh2.x, 1e-30f)), rsqrtf(fmaxf(qh2.y, 1e-30f)));
             const float2 cphi = mul2(fma2(dup(A.wcos), qx, mul2(dup(A.wsin), qy)), rq);
             float2 nq;
             if constexpr (CWM)
@@ -952,8 +957,9 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
             const float2 nqp = make_float2(fmaxf(nq.x, 0.0f), fmaxf(nq.y, 0.0f));
             float2 X = mul2(mul2(G.base_area, fma2(dup(A.wind_mod), cphi, one)), mul2(nqp, inv_n));
             if constexpr (CWM) X = mul2(X, areaf);
+            // X >= 0 and Q_z > 0: X rsqrt(X Q_z), clamped so that X = 0 gives 0
             const float2 Xq = mul2(X, qz);
-            amp_s = make_float2(X.x > 0.0f ? X.x * rsqrtf(Xq.x) : 0.0f, X.y > 0.0f ? X.y * rsqrtf(Xq.y) : 0.0f);
+            amp_s = mul2(X, make_float2(rsqrtf(fmaxf(Xq.x, 1e-30f)), rsqrtf(fmaxf(Xq.y, 1e-30f))));
         } else if constexpr (CWM) {
             amp_s = mul2(amp_s, make_float2(sqrtf(areaf.x), sqrtf(areaf.y)));
         }
