@@ -119,22 +119,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# Work per contribution of the mixed accumulator (FP32 flops: FFMA2 = 4, FFMA and
-# FMUL2/FADD2 = 2, FMUL/FADD = 1): the formulation's arithmetic as counted by the
-# instruction-mix counters on the 512-pulse capture of the headline scene (per
-# contribution 69.0 FFMA2 + 13.0 FFMA + 15.7 FMUL2 + 19.8 FMUL + 15.0 FADD2 + 3.3
-# FADD), with the generator's time-Taylor contraction amortised over 128 pulses and
-# 6 channels.
-FLOPS_PER_CONTRIBUTION = 386.6
+# Algorithmic FP32 work per contribution, frozen from the formulation before any
+# tuning: the accumulator's per-(facet, pulse, channel) arithmetic (geometry,
+# patterns, NRCS, phase, 8 taps, bin add: 150 flops) plus the surface generator's
+# direct synthesis of (eta, eta_x, eta_y) from 256 components (1536 FMA = 3072
+# flops per facet and pulse), shared by the channels.
+ALGO_FLOPS_ACCUMULATOR = 150.0
+ALGO_FLOPS_GENERATOR_PER_FACET_PULSE = 3072.0
+# What the kernel executes per contribution, from the instruction-mix counters on
+# the 512-pulse capture of the headline scene (FFMA2 = 4 flops, FFMA / FMUL2 /
+# FADD2 = 2, FMUL / FADD = 1; per contribution 37.8 FFMA2 + 22.0 FFMA + 13.7 FMUL2
+# + 11.8 FMUL + 9.2 FADD2 + 1.5 FADD): the time-Taylor generator replaces the
+# direct synthesis, so this is far below the algorithmic count.
+EXECUTED_FLOPS_PER_CONTRIBUTION = 254.6
 # All instructions issued per contribution (thread level, same capture).
-INSTR_PER_CONTRIBUTION = 355.9
+INSTR_PER_CONTRIBUTION = 242.5
 # DRAM bytes (read + write) of one headline launch (2048 pulses), from one ncu
 # capture of dram__bytes_read.sum + dram__bytes_write.sum, and the SHA-256 of the
 # kernel sources it was taken on: the figure is reported only while they match.
-TRAFFIC_BYTES = 81734400 + 29260032
+TRAFFIC_BYTES = 81427456 + 26758912
 TRAFFIC_PULSES = 2048
-TRAFFIC_SOURCES = ("echo_mixed.cu", "harm_kernels.cuh", "harm_internal.cuh")
-TRAFFIC_SHA256 = "0c2cda365086c3921490c70fd1890b059fb46987f1b844bfe73de1592a3a6dbf"
+TRAFFIC_SOURCES = ("echo_mixed.cuh", "harm_kernels.cuh", "harm_internal.cuh")
+TRAFFIC_SHA256 = "db805e4f241dd85508049429caf86bc029b0e77d8224169ba9bb586092883d34"
 
 
 def captured_traffic(np_step):
@@ -304,11 +310,13 @@ def main():
             dist.destroy_process_group()
         return
 
-    flops = FLOPS_PER_CONTRIBUTION * units
+    algo_per_unit = ALGO_FLOPS_ACCUMULATOR + ALGO_FLOPS_GENERATOR_PER_FACET_PULSE / nc
+    flops = algo_per_unit * units
     peaks = measured_peaks()
     sm_max = (peaks or {}).get("sm_max_mhz", 2032.0)
     fp32_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, unit counts x max SM clock
     achieved = flops / (kern_ms * 1e-3) / 1e12
+    executed = EXECUTED_FLOPS_PER_CONTRIBUTION * units / (kern_ms * 1e-3) / 1e12
     issue_peak = 148 * 4 * 32 * sm_max * 1e6  # thread instructions / s
     issue_frac = INSTR_PER_CONTRIBUTION * units / (kern_ms * 1e-3) / issue_peak
 
@@ -328,10 +336,16 @@ def main():
                      "frac": achieved / fp32_peak if prec == harm.HARM_PREC_MIXED else None,
                      "traffic": captured_traffic(np_step) if prec == harm.HARM_PREC_MIXED else None,
                      "kernel": "accumulate_mixed_kernel" if prec == harm.HARM_PREC_MIXED else "accumulate_f64_kernel",
-                     "kernel_ms": kern_ms, "flops_per_contribution": flops / units,
+                     "kernel_ms": kern_ms, "flops_per_contribution": algo_per_unit,
+                     "flops_basis": "algorithmic: %.0f accumulator + %.0f / %d channels generator (direct "
+                                    "256-component synthesis) per contribution" % (
+                                        ALGO_FLOPS_ACCUMULATOR, ALGO_FLOPS_GENERATOR_PER_FACET_PULSE, nc),
                      "peak_basis": "148 SM x 128 FP32 lanes x 2 x %.0f MHz (max SM clock)" % sm_max,
+                     "executed_flops_per_contribution": EXECUTED_FLOPS_PER_CONTRIBUTION,
+                     "executed_tflops": executed if prec == harm.HARM_PREC_MIXED else None,
+                     "executed_frac": executed / fp32_peak if prec == harm.HARM_PREC_MIXED else None,
                      "issue_frac": issue_frac,
-                     "issue_basis": "%.0f thread instructions per contribution vs 148 SM x 4 x 32 per clock"
+                     "issue_basis": "%.1f thread instructions per contribution vs 148 SM x 4 x 32 per clock"
                                     % INSTR_PER_CONTRIBUTION},
         "clocks": clk,
         "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
