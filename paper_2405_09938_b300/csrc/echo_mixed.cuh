@@ -791,8 +791,31 @@ struct GatherSink2 {
         const float2 *wc = win + ch * WT;
         const int tb = kbase - WT_LO;
         const InT *grow = resid + 2 * ((size_t)ch * np + (n - n0)) * A.S.nr;
-        const float2 ga = gather(A, wc, tb, grow, kba, ha);
-        const float2 gb = gather(A, wc, tb, grow, kbb, hb);
+        float2 ga, gb;
+        const int k0 = min(kba, kbb), w0 = k0 - tb;
+        if (abs(kbb - kba) <= 1 && w0 >= 0 && w0 + 8 < WT) {
+            // both facets' bins lie in k0 .. k0 + 8 inside the window: read the 9
+            // residual values once and gather both facets from them
+            const bool sa = kba != k0, sb = kbb != k0;
+            float2 v[9];
+#pragma unroll
+            for (int j = 0; j < 9; ++j) v[j] = wc[w0 + j];
+            float gar = 0.0f, gai = 0.0f, gbr = 0.0f, gbi = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const float a = sa ? (j > 0 ? ha[j - 1] : 0.0f) : (j < 8 ? ha[j] : 0.0f);
+                const float b = sb ? (j > 0 ? hb[j - 1] : 0.0f) : (j < 8 ? hb[j] : 0.0f);
+                gar = fmaf(a, v[j].x, gar);
+                gai = fmaf(a, v[j].y, gai);
+                gbr = fmaf(b, v[j].x, gbr);
+                gbi = fmaf(b, v[j].y, gbi);
+            }
+            ga = make_float2(gar, gai);
+            gb = make_float2(gbr, gbi);
+        } else {
+            ga = gather(A, wc, tb, grow, kba, ha);
+            gb = gather(A, wc, tb, grow, kbb, hb);
+        }
         const float2 GR = make_float2(ga.x, gb.x), GI = make_float2(ga.y, gb.y);
         const float2 re_gs = fma2(GR, vre, mul2(GI, vim));
         const float2 im_gs = fma2(GR, vim, neg2(mul2(GI, vre)));
@@ -803,7 +826,7 @@ struct GatherSink2 {
     }
 };
 
-// Per-thread pair of facets (same column, rows w and w + 8) for the packed path.
+// Per-thread pair of facets (same column, adjacent rows) for the packed path.
 struct PairGeo {
     float2 xi_y, fj, base_area, amp_static, cu, cv, zr, zi;
     bool va, vb;
