@@ -58,6 +58,7 @@ constexpr int WCH = 128;      // wave components per shared-memory chunk
 constexpr int SROW = 72;      // floats per bin row of the warp buffer (2 halves of 32 + pad)
 constexpr int SHALF = 36;     // float offset of lanes 16..31 in a row
 constexpr int SBINS = 16;     // bins per warp window
+constexpr int kTileBufs = 4;  // CTA range tiles in flight (a ring over consecutive pulses)
 constexpr float kPiF = 3.14159265358979f;
 
 // Variant bits of the per-pulse code.
@@ -167,7 +168,7 @@ __host__ __device__ inline Layout layout(int nc, bool dup, int nf)
     L.w = o;
     L.stage = o;
     o += wbytes > sbytes ? wbytes : sbytes;
-    L.tile = o = align16(o);  o += 2 * nc * WT * 8;
+    L.tile = o = align16(o);  o += kTileBufs * nc * WT * 8;
     L.tx = o = align16(o);    o += NBR * (int)(dup ? sizeof(AntRec2) : sizeof(AntRec));
     L.rx = o = align16(o);    o += NBR * nc * (int)(dup ? sizeof(AntRec2) : sizeof(AntRec));
     L.ch = o = align16(o);    o += NBR * nc * (int)(dup ? sizeof(ChanRec2) : sizeof(ChanRec));
@@ -183,7 +184,7 @@ __host__ __device__ inline Layout layout(int nc, bool dup, int nf)
 
 struct Smem {
     float2 *w;       // [WCH][3][kOrders]
-    float2 *tile;    // [2][nc][WT]
+    float2 *tile;    // [kTileBufs][nc][WT]
     AntRec *tx;      // [NBR]          (scalar layout: adjoint)
     AntRec *rx;      // [NBR][nc]
     ChanRec *ch;     // [NBR][nc]
@@ -737,7 +738,7 @@ struct FacetGeo {
 template <typename OutT>
 struct ScatterSink {
     float *stage;
-    float2 *tiles;  // [2][nc][WT]
+    float2 *tiles;  // [kTileBufs][nc][WT]
     OutT *iq;
     int n, n0, np, buf;
     // two facets (packed path): one warp reduction each
@@ -1258,33 +1259,39 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
             G.zi = make_float2(ga.z.y, two ? gb.z.y : 0.0f);
             for (; n < ne; ++n) {
                 const int pi = n - c0;
-                const int buf = n & 1;
                 sink.n = n;
-                sink.buf = buf;
+                sink.buf = n & (kTileBufs - 1);
                 float2 st[NF];
                 eval_state<NF>(sm, C, sm.pr[pi].tau, st);
                 facet_pulse2<TAPS, V>(sm, A, P, G, st, pi, xi_x, fi, sink);
-                __syncthreads();
-                for (int i = threadIdx.x; i < nc * WT; i += NT) {
-                    int ch = i / WT, w = i % WT;
-                    float2 *slot = sm.tile + (buf * nc + ch) * WT + w;
-                    float2 v = *slot;
-                    *slot = make_float2(0.f, 0.f);
-                    int k = sm.ch2[pi * nc + ch].kbase - WT_LO + w;
-                    if ((v.x != 0.0f || v.y != 0.0f) && k >= 0 && k < S.nr)
-                        gadd<OutT>(iq + 2 * ((size_t)ch * np + (n - n0)) * S.nr, (size_t)k, v.x, v.y);
+                // flush the range tiles of pulse pairs (one barrier per two pulses;
+                // a tile is reused four pulses later, after at least one more barrier)
+                if ((pi & 1) || n == ce - 1) {
+                    __syncthreads();
+                    for (int p = (pi & 1) ? n - 1 : n; p <= n; ++p) {
+                        const int pp = p - c0, pb = p & (kTileBufs - 1);
+                        for (int i = threadIdx.x; i < nc * WT; i += NT) {
+                            int ch = i / WT, w = i % WT;
+                            float2 *slot = sm.tile + (pb * nc + ch) * WT + w;
+                            float2 v = *slot;
+                            *slot = make_float2(0.f, 0.f);
+                            int k = sm.ch2[pp * nc + ch].kbase - WT_LO + w;
+                            if ((v.x != 0.0f || v.y != 0.0f) && k >= 0 && k < S.nr)
+                                gadd<OutT>(iq + 2 * ((size_t)ch * np + (p - n0)) * S.nr, (size_t)k, v.x, v.y);
+                        }
+                    }
                 }
             }
         }
     }
-    // the other buffer was flushed one pulse earlier; make sure every thread is
-    // done with the tiles and the records before they are reused
+    // every tile has been flushed; make sure every thread is done with the tiles
+    // and the records before they are reused
     __syncthreads();
 }
 
 __device__ __forceinline__ void clear_smem(const Smem &sm, int nc)
 {
-    for (int i = threadIdx.x; i < 2 * nc * WT; i += NT) sm.tile[i] = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < kTileBufs * nc * WT; i += NT) sm.tile[i] = make_float2(0.f, 0.f);
     for (int i = threadIdx.x; i < NWARP * SBINS * SROW; i += NT) sm.stage[i] = 0.0f;
 }
 
