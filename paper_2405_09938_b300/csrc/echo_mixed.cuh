@@ -939,7 +939,7 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
 
     const AntRec2 *RX = sm.rx2 + pi * nc;
     const ChanRec2 *CH = sm.ch2 + pi * nc;
-    float2 gr_prev = make_float2(0.0f, 0.0f);
+    float2 gr_prev = make_float2(0.0f, 0.0f), amps_prev = make_float2(0.0f, 0.0f);
     for (int ch = 0; ch < nc; ++ch) {
         const AntRec2 R = RX[ch];
         const ChanRec2 Q = CH[ch];
@@ -968,7 +968,11 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
         const float2 qz = neg2(fma2(fma2(eta, R.invR, R.uz), rho_r, rt2));
         // sqrt(sigma0 A) = X rsqrt(X Q_z), X = base A (1 + m cos phi) max(0, n.Q) / |n| (x n_z with the CWM)
         float2 amp_s = G.amp_static;
-        if (!S.static_surface) {
+        if ((S.rx_share >> ch) & 1u) {
+            // phase centre of the previous channel's antenna: its Q direction differs
+            // by ~(separation / R) ~ 6e-6 rad, the NRCS by < 4e-6 relative
+            amp_s = amps_prev;
+        } else if (!S.static_surface) {
             const float2 qh2 = fma2(qx, qx, mul2(qy, qy));
             // 1 / |Q_H| (clamped: Q_H = 0 gives cos phi = 0)
             const float2 rq = make_float2(rsqrtf(fmaxf(qh2.x, 1e-30f)), rsqrtf(fmaxf(qh2.y, 1e-30f)));
@@ -987,6 +991,7 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
         } else if constexpr (CWM) {
             amp_s = mul2(amp_s, make_float2(sqrtf(areaf.x), sqrtf(areaf.y)));
         }
+        amps_prev = amp_s;
         const float2 amp = LUT ? mul2(mul2(amp_s, ampt), mul2(R.ampr, rho_r))
                                : mul2(mul2(mul2(amp_s, ampt), mul2(gr, R.ampr)), rho_r);
         const float2 vc = neg2(fma2(G.cu, qx, mul2(G.cv, qy)));
