@@ -643,10 +643,39 @@ __device__ __forceinline__ void warp_scatter(float *buf, float2 *tile_c, int til
 // pass needs every lane's first bins within one of each other and all lanes' k0
 // within 7 bins; otherwise it returns false and the caller reduces the facets one
 // at a time.
+// Window of one pair reduction, decided as soon as the bins are known (the warp
+// reductions then overlap the rest of the per-channel arithmetic).
+struct PairPlan {
+    int kmin;  // first bin of the warp window; INT_MAX when no facet of the warp is valid
+    int span;  // rows of the window in use
+    bool ok;   // the single-pass form applies
+};
+
+__device__ __forceinline__ PairPlan plan_pair(int kba, int kbb, bool va, bool vb)
+{
+    const unsigned FULL = 0xffffffffu;
+    if (!va) kba = kbb;
+    if (!vb) kbb = kba;
+    const bool valid = va || vb;
+    const int k0 = min(kba, kbb);
+    PairPlan pl;
+    pl.kmin = __reduce_min_sync(FULL, valid ? k0 : INT_MAX);
+    pl.span = 0;
+    pl.ok = true;
+    if (pl.kmin == INT_MAX) return pl;
+    // one reduction serves the window check: the lane's row offset, or a value
+    // beyond the window when its two facets' first bins are more than one apart
+    const int omax = __reduce_max_sync(FULL, valid ? (abs(kbb - kba) > 1 ? 1 << 20 : k0 - pl.kmin) : 0);
+    pl.ok = omax <= SBINS - 9;
+    pl.span = omax + 9;
+    return pl;
+}
+
 template <typename OutT>
-__device__ __forceinline__ bool warp_scatter_pair(float *buf, float2 *tile_c, int tile_base, int kba, int kbb,
-                                                  bool va, bool vb, const float ha[8], const float hb[8], float2 vre,
-                                                  float2 vim, int nr, OutT *grow, unsigned int *flags)
+__device__ __forceinline__ void warp_scatter_pair(const PairPlan &pl, float *buf, float2 *tile_c, int tile_base,
+                                                  int kba, int kbb, bool va, bool vb, const float ha[8],
+                                                  const float hb[8], float2 vre, float2 vim, int nr, OutT *grow,
+                                                  unsigned int *flags)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -662,10 +691,7 @@ __device__ __forceinline__ bool warp_scatter_pair(float *buf, float2 *tile_c, in
     }
     const bool valid = va || vb;
     const int k0 = min(kba, kbb);
-    const int kmin = __reduce_min_sync(FULL, valid ? k0 : INT_MAX);
-    if (kmin == INT_MAX) return true;
-    const int kmax = __reduce_max_sync(FULL, valid ? k0 : INT_MIN);
-    if (kmax - kmin > SBINS - 9 || __any_sync(FULL, valid && abs(kbb - kba) > 1)) return false;
+    const int kmin = pl.kmin;
     const int o = k0 - kmin;
     const int ll = lane & 15;
     const int hbase = lane < 16 ? 0 : SHALF;
@@ -686,7 +712,7 @@ __device__ __forceinline__ bool warp_scatter_pair(float *buf, float2 *tile_c, in
     __syncwarp();
     const int w = lane >> 1, half = lane & 1;
     float ar = 0.0f, ai = 0.0f;
-    if (w < kmax - kmin + 9) {
+    if (w < pl.span) {
         const float4 *rp = reinterpret_cast<const float4 *>(buf + w * SROW + half * SHALF);
         float4 v[8];
 #pragma unroll
@@ -718,7 +744,6 @@ __device__ __forceinline__ bool warp_scatter_pair(float *buf, float2 *tile_c, in
             atomicAdd(flags + 2, 1u);
         }
     }
-    return true;
 }
 
 struct FacetGeo {
@@ -741,17 +766,24 @@ struct ScatterSink {
     float2 *tiles;  // [kTileBufs][nc][WT]
     OutT *iq;
     int n, n0, np, buf;
-    // two facets (packed path): one warp reduction each
+    PairPlan plan;
+    // the bins of the channel's two facets are known: plan the warp window
+    __device__ __forceinline__ void prepare(int kba, int kbb, bool va, bool vb) { plan = plan_pair(kba, kbb, va, vb); }
+    // the two facets' taps and values: one warp reduction for both, or one each
+    // when the single-pass form does not apply
     __device__ __forceinline__ void put2(const MixedArgs &A, int ch, int kbase, int kba, int kbb, const float ha[8],
                                          const float hb[8], float2 vre, float2 vim, float2, float2, float, bool va,
                                          bool vb)
     {
+        if (plan.kmin == INT_MAX) return;
         float2 *tile_c = tiles + (buf * A.S.nc + ch) * WT;
         const int tile_base = kbase - WT_LO;
         OutT *grow = iq + 2 * ((size_t)ch * np + (n - n0)) * A.S.nr;
-        if (warp_scatter_pair<OutT>(stage, tile_c, tile_base, kba, kbb, va, vb, ha, hb, vre, vim, A.S.nr, grow,
-                                    A.S.flags))
+        if (plan.ok) {
+            warp_scatter_pair<OutT>(plan, stage, tile_c, tile_base, kba, kbb, va, vb, ha, hb, vre, vim, A.S.nr, grow,
+                                    A.S.flags);
             return;
+        }
         warp_scatter<OutT>(stage, tile_c, tile_base, kba, va, ha, vre.x, vim.x, A.S.nr, grow, A.S.flags);
         warp_scatter<OutT>(stage, tile_c, tile_base, kbb, vb, hb, vre.y, vim.y, A.S.nr, grow, A.S.flags);
     }
@@ -765,6 +797,7 @@ struct GatherSink2 {
     const InT *resid;
     int n, n0, np;
     float2 as, au, av;  // per-facet accumulators, facet a in .x, facet b in .y
+    __device__ __forceinline__ void prepare(int, int, bool, bool) {}
     __device__ __forceinline__ float2 gather(const MixedArgs &A, const float2 *wc, int tb, const InT *grow, int kb,
                                              const float h[8]) const
     {
@@ -947,6 +980,14 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
         const float2 sr_ = fma2(neg2(ar), ar, b2);
         const float2 qr = mul2(sr_, fma2(neg2(ar), R.inv2R2, R.inv2R));
         const float2 dr = add2(ar, qr);
+        // range bins first: the warp window of the reduction is planned here, its
+        // warp-wide reductions overlapping the pattern, NRCS and phase arithmetic
+        const float2 p = fma2(add2(dt, dr), dup(A.inv_dr), Q.pfrac);
+        const float2 kf = make_float2(floorf(p.x), floorf(p.y));
+        const float2 fr = sub2(p, kf);
+        const int kba = Q.kbase + (int)kf.x - (TAPS == 1 ? 0 : 3);
+        const int kbb = Q.kbase + (int)kf.y - (TAPS == 1 ? 0 : 3);
+        sink.prepare(kba, kbb, G.va, G.vb);
         const float2 er = mul2(dr, R.invR);
         const float2 rho_r = fma2(er, er, sub2(one, er));
         float2 gr, gri;
@@ -1022,20 +1063,12 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
         }
         const float2 vre = fma2(zr, cp, neg2(mul2(zi, sp)));
         const float2 vim = fma2(zr, sp, mul2(zi, cp));
-        const float2 p = fma2(add2(dt, dr), dup(A.inv_dr), Q.pfrac);
-        const float2 kf = make_float2(floorf(p.x), floorf(p.y));
-        const float2 fr = sub2(p, kf);
-        int kba, kbb;
         float ha[8], hb[8];
         if (TAPS == 1) {
-            kba = Q.kbase + (int)kf.x;
-            kbb = Q.kbase + (int)kf.y;
             ha[0] = hb[0] = 1.0f;
 #pragma unroll
             for (int j = 1; j < 8; ++j) ha[j] = hb[j] = 0.0f;
         } else {
-            kba = Q.kbase + (int)kf.x - 3;
-            kbb = Q.kbase + (int)kf.y - 3;
             const float2 t = fma2(dup(2.0f), fr, dup(-1.0f));
             const float2 t2 = mul2(t, t);
 #pragma unroll
