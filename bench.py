@@ -128,19 +128,19 @@ ALGO_FLOPS_ACCUMULATOR = 150.0
 ALGO_FLOPS_GENERATOR_PER_FACET_PULSE = 3072.0
 # What the kernel executes per contribution, from the instruction-mix counters on
 # the 512-pulse capture of the headline scene (FFMA2 = 4 flops, FFMA / FMUL2 /
-# FADD2 = 2, FMUL / FADD = 1; per contribution 37.8 FFMA2 + 22.0 FFMA + 13.7 FMUL2
-# + 11.8 FMUL + 9.2 FADD2 + 1.5 FADD): the time-Taylor generator replaces the
+# FADD2 = 2, FMUL / FADD = 1; per contribution 35.6 FFMA2 + 22.0 FFMA + 11.0 FMUL2
+# + 11.7 FMUL + 9.2 FADD2 + 1.5 FADD): the time-Taylor generator replaces the
 # direct synthesis, so this is far below the algorithmic count.
-EXECUTED_FLOPS_PER_CONTRIBUTION = 254.6
+EXECUTED_FLOPS_PER_CONTRIBUTION = 240.2
 # All instructions issued per contribution (thread level, same capture).
-INSTR_PER_CONTRIBUTION = 242.5
+INSTR_PER_CONTRIBUTION = 233.8
 # DRAM bytes (read + write) of one headline launch (2048 pulses), from one ncu
 # capture of dram__bytes_read.sum + dram__bytes_write.sum, and the SHA-256 of the
 # kernel sources it was taken on: the figure is reported only while they match.
-TRAFFIC_BYTES = 81427456 + 26758912
+TRAFFIC_BYTES = 81211136 + 24608256
 TRAFFIC_PULSES = 2048
 TRAFFIC_SOURCES = ("echo_mixed.cuh", "harm_kernels.cuh", "harm_internal.cuh")
-TRAFFIC_SHA256 = "db805e4f241dd85508049429caf86bc029b0e77d8224169ba9bb586092883d34"
+TRAFFIC_SHA256 = "3582c3a20a75b6b59ea25d6ac6f6c8180581b18e06890a110f7b9d63ea514f2d"
 
 
 def captured_traffic(np_step):
