@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-scene batched measurement")
+    ap.add_argument("--no-generator", action="store_true", help="skip the standalone facet-generator timing")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the timing of the surface and scattering variants")
     return ap.parse_args()
@@ -358,6 +359,8 @@ def main():
         line["batched"] = measure_batched(args, stream)
     if prec == harm.HARM_PREC_MIXED and not args.no_variants:
         line["variants"] = measure_variants(args, stream, flush)
+    if prec == harm.HARM_PREC_MIXED and not args.no_generator:
+        line["generator"] = measure_generator(args, stream, flush)
     if not args.no_cpu:
         cpu = run_oracle_sample(desc, args.cpu_pulses)
         # IQ error of the GPU path on the sampled pulses
@@ -462,6 +465,44 @@ def measure_batched(args, stream):
             "ms": ms, "value": units / (ms * 1e-3), "launches": 1, "graph": True,
             "tile_rows": {"8": rows.count(8), "16": rows.count(16)},
             "scene_create_s": create_s, "tune_s": tune_s}
+
+
+def measure_generator(args, stream, flush):
+    """The facet generator on its own (harm_facets_generate): states (eta, eta_x,
+    eta_y) of every facet of the headline scene for one 128-pulse window, written
+    to HBM as float32 [128][3][n_facets] (3.07 GB); one warm-up, then the mean of
+    three timed runs, L2 flushed before each. Bound by the HBM write stream."""
+    import torch
+    from paper_2405_09938_b300 import harm
+    d = hs.ati_scene()
+    scene = harm.harm_scene_create(d, harm.HARM_PREC_MIXED, stream)
+    npw = 128
+    st = torch.empty((npw, 3, d["ny"], d["nx"]), dtype=torch.float32, device="cuda")
+    times = []
+    for i in range(4):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        harm.harm_facets_generate(scene, 0, npw, st)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            times.append(a.elapsed_time(b))
+    harm.harm_scene_sync(scene)
+    scene.close()
+    ms = statistics.mean(times)
+    nbytes = st.numel() * st.element_size()
+    del st
+    torch.cuda.empty_cache()
+    peaks = measured_peaks() or {}
+    hbm = peaks.get("hbm_gbs")
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"workload": "ati_4x2km_states_128p", "facet_pulses": hs.n_facets(d) * npw, "ms": ms,
+            "value": hs.n_facets(d) * npw / (ms * 1e-3), "unit": "facet-pulse states/s",
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": gbs / hbm if hbm else None,
+                         "bytes": nbytes, "bytes_basis": "states written (float32, 3 fields); wave tables are "
+                                                         "L2-resident"}}
 
 
 def measure_variants(args, stream, flush):
