@@ -427,7 +427,7 @@ __device__ __forceinline__ float het_weight(const DevScene &S, int cx, int cy, i
 // rows iya / iyb), accumulated over the wave components of every wave set in R
 // (weighted per facet by Eq. 2 for a heterogeneous sea state), the time tables
 // staged in shared-memory chunks.
-template <int NF, bool HET>
+template <int NF, bool HET, int UNROLL>
 __device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int ix, int iya, int iyb, bool two,
                               const SetRange &R, float ca[NF][kOrders], float cb[NF][kOrders])
 {
@@ -451,6 +451,7 @@ __device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int
                 for (int i = threadIdx.x; i < cnt * NF * kOrders; i += NT) sm.w[i] = src[i];
                 __syncthreads();
                 if (wa == 0.0f && (!two || wb == 0.0f)) continue;
+#pragma unroll UNROLL
                 for (int m = 0; m < cnt; ++m) {
                     const size_t qm = qw + m0 + m;
                     float2 e = __ldg(A.ex + qm * S.nx + ixc);
@@ -1165,8 +1166,10 @@ __device__ __forceinline__ void stage_luts(const Smem &sm, const DevScene &S)
 }
 
 // Taylor coefficients of the item's two facets per thread, or zero for a static
-// surface.
-template <int NF>
+// surface. UNROLL unrolls the component loop (the standalone generator, which does
+// little else, hides the table loads that way; the echo kernels keep their
+// registers for the pulse loop).
+template <int NF, int UNROLL = 1>
 __device__ __forceinline__ void item_coeffs(const Smem &sm, const MixedArgs &A, int batch, int tx0, int ty0, int ty,
                                             int ix, int iya, int iyb, bool two, float ca[NF][kOrders],
                                             float cb[NF][kOrders])
@@ -1175,9 +1178,9 @@ __device__ __forceinline__ void item_coeffs(const Smem &sm, const MixedArgs &A, 
     if (!S.static_surface && S.nw > 0) {
         const SetRange R = set_range(S, tx0, tx0 + TX - 1, ty0, ty0 + ty - 1);
         if (S.het_ncx > 0)
-            taylor_coeffs<NF, true>(sm, A, batch, ix, iya, iyb, two, R, ca, cb);
+            taylor_coeffs<NF, true, UNROLL>(sm, A, batch, ix, iya, iyb, two, R, ca, cb);
         else
-            taylor_coeffs<NF, false>(sm, A, batch, ix, iya, iyb, two, R, ca, cb);
+            taylor_coeffs<NF, false, UNROLL>(sm, A, batch, ix, iya, iyb, two, R, ca, cb);
     } else {
 #pragma unroll
         for (int f = 0; f < NF; ++f)
@@ -1570,7 +1573,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     const int iya = ty0 + 2 * warp, iyb = iya + 1;
     const bool va = ix < S.nx && iya < S.ny, vb = ix < S.nx && iyb < S.ny;
     float ca[NF][kOrders], cb[NF][kOrders];
-    item_coeffs<NF>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, true, ca, cb);
+    item_coeffs<NF, 4>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, true, ca, cb);
     const int64_t nf = (int64_t)S.nx * S.ny;
     for (int n = pa; n < pe; ++n) {
         float tau = A.tau[n];
