@@ -3,7 +3,8 @@ configuration the bench times, on outputs the FP64 oracle can compute one by one
 
 * the headline ATI scene (2000 x 1000 facets, 2048 pulses, 6 channels, complex64,
   one launch over the whole burst): IQ relative RMS and ATI phase bias on 3
-  sampled pulses, all channels and range samples;
+  sampled pulses, all channels and range samples, and the error of the FP32
+  accumulation stage (complex64 against complex128 output of the same run);
 * the 48-scene batch (one persistent graph-replayed launch after tuning): one
   pulse of the smallest and of the largest scene;
 * the differentiable scene (1000 x 500 facets, 6 channels, 100 m cells): the
@@ -49,6 +50,27 @@ def test_headline_scene_full_burst_sampled_pulses():
         assert rel_rms(got[c], want[c]) < TOL_MIXED
     for a, b in ((0, 1), (1, 2), (3, 4), (4, 5)):
         assert abs(ati_phase_bias(got, want, a, b)) < 1e-4
+
+
+def test_headline_complex64_accumulation_error():
+    # the FP32 warp and tile sums are common to both outputs; the complex64 output
+    # also adds the tiles into the IQ in FP32 (atomics), the complex128 output in
+    # FP64: their difference bounds the error of the FP32 accumulation stage
+    import torch
+    d = hs.ati_scene()
+    sc = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
+    pulses = [5, 1500]
+    outs = []
+    for dt in (torch.complex64, torch.complex128):
+        iq = torch.zeros((6, d["n_pulses"], d["n_range"]), dtype=dt, device="cuda")
+        harm.harm_echo_accumulate(sc, 0, d["n_pulses"], iq)
+        harm.harm_scene_sync(sc)
+        outs.append(iq[:, pulses, :].cpu().numpy().astype(np.complex128))
+        del iq
+    sc.close()
+    err = rel_rms(outs[0], outs[1])
+    print("complex64 vs complex128 accumulation: rel RMS %.3e" % err)
+    assert err < 2e-6
 
 
 def test_batch_of_48_scenes_full_size_sampled():
