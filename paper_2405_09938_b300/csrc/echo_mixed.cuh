@@ -52,6 +52,10 @@ constexpr int NT = 256;       // threads per CTA
 constexpr int NWARP = NT / 32;
 constexpr int WT = 48;        // range bins per channel in the CTA tile
 constexpr int WT_LO = 22;     // tile window starts WT_LO bins below the reference bin
+constexpr int WA = 32;        // range bins per channel of the adjoint's residual window
+constexpr int WA_LO = 14;     // (a 32 x 16 facet tile spans about +-10 bins around its
+                              // reference bin, taps and heights included; residuals
+                              // outside the window are read from global memory)
 constexpr int NBR = 16;       // pulses per chunk of FP64 tile references
 constexpr int NBG = 128;      // pulses per work item (time-Taylor window of the generator)
 constexpr int WCH = 128;      // wave components per shared-memory chunk
@@ -794,7 +798,7 @@ struct ScatterSink {
 // chain-rule terms accumulated as pairs.
 template <typename InT>
 struct GatherSink2 {
-    const float2 *win;  // [nc][WT] residual window of the pulse
+    const float2 *win;  // [nc][WA] residual window of the pulse
     const InT *resid;
     int n, n0, np;
     float2 as, au, av;  // per-facet accumulators, facet a in .x, facet b in .y
@@ -808,7 +812,7 @@ struct GatherSink2 {
             const int k = kb + j;
             const int w = k - tb;
             float2 v;
-            if ((unsigned)w < (unsigned)WT)
+            if ((unsigned)w < (unsigned)WA)
                 v = wc[w];
             else if (k >= 0 && k < A.S.nr)
                 v = make_float2((float)grow[2 * k], (float)grow[2 * k + 1]);
@@ -823,12 +827,12 @@ struct GatherSink2 {
                                          const float hb[8], float2 vre, float2 vim, float2 qx, float2 qy, float k0t,
                                          bool, bool)
     {
-        const float2 *wc = win + ch * WT;
-        const int tb = kbase - WT_LO;
+        const float2 *wc = win + ch * WA;
+        const int tb = kbase - WA_LO;
         const InT *grow = resid + 2 * ((size_t)ch * np + (n - n0)) * A.S.nr;
         float2 ga, gb;
         const int k0 = min(kba, kbb), w0 = k0 - tb;
-        if (abs(kbb - kba) <= 1 && w0 >= 0 && w0 + 8 < WT) {
+        if (abs(kbb - kba) <= 1 && w0 >= 0 && w0 + 8 < WA) {
             // both facets' bins lie in k0 .. k0 + 8 inside the window: read the 9
             // residual values once and gather both facets from them
             const bool sa = kba != k0, sb = kbb != k0;
@@ -1529,9 +1533,9 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
                 const int pi = n - c0;
                 __syncthreads();  // the previous pulse is done with the residual window
                 // residual window of this pulse, every channel
-                for (int i = threadIdx.x; i < nc * WT; i += NT) {
-                    int ch = i / WT, w = i % WT;
-                    int k = sm.ch2[pi * nc + ch].kbase - WT_LO + w;
+                for (int i = threadIdx.x; i < nc * WA; i += NT) {
+                    int ch = i / WA, w = i % WA;
+                    int k = sm.ch2[pi * nc + ch].kbase - WA_LO + w;
                     float2 v = make_float2(0.f, 0.f);
                     if (k >= 0 && k < S.nr) {
                         const InT *r = resid + 2 * (((size_t)ch * np + (n - n0)) * S.nr + k);
