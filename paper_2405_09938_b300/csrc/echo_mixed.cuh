@@ -119,7 +119,7 @@ struct __align__(16) ChanRec2 {
 
 // u-v gain grid of one antenna in FP32 (shared memory copy of the descriptor).
 struct PatLutF {
-    const float2 *g;  // [nv][nu]
+    const float4 *g;  // [nv][nu - 1] node pairs
     int nu, nv;
     float u0, inv_du, v0, inv_dv;
     float umax, vmax;  // nu - 1, nv - 1
@@ -887,10 +887,11 @@ __device__ __forceinline__ float2 lut_gain_f(const PatLutF &L, float u, float v)
     if (!(fu >= 0.0f && fu <= L.umax && fv >= 0.0f && fv <= L.vmax)) return make_float2(0.0f, 0.0f);
     const int iu = min((int)fu, L.nu - 2), iv = min((int)fv, L.nv - 2);
     const float a = fu - (float)iu, b = fv - (float)iv;
-    const float2 *g = L.g + (size_t)iv * L.nu + iu;
-    const float2 g00 = __ldg(g), g10 = __ldg(g + 1), g01 = __ldg(g + L.nu), g11 = __ldg(g + L.nu + 1);
-    const float2 lo = make_float2(fmaf(a, g10.x - g00.x, g00.x), fmaf(a, g10.y - g00.y, g00.y));
-    const float2 hi = make_float2(fmaf(a, g11.x - g01.x, g01.x), fmaf(a, g11.y - g01.y, g01.y));
+    // node pairs (g[iv][iu], g[iv][iu + 1]) and (g[iv + 1][iu], g[iv + 1][iu + 1])
+    const float4 *g = L.g + (size_t)iv * (L.nu - 1) + iu;
+    const float4 r0 = __ldg(g), r1 = __ldg(g + (L.nu - 1));
+    const float2 lo = make_float2(fmaf(a, r0.z - r0.x, r0.x), fmaf(a, r0.w - r0.y, r0.y));
+    const float2 hi = make_float2(fmaf(a, r1.z - r1.x, r1.x), fmaf(a, r1.w - r1.y, r1.y));
     return make_float2(fmaf(b, hi.x - lo.x, lo.x), fmaf(b, hi.y - lo.y, lo.y));
 }
 

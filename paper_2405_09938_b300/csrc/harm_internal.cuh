@@ -41,7 +41,7 @@ struct PatLut {
     int nu, nv;
     double u0, inv_du, v0, inv_dv;
     const double2 *g64;  // [nv][nu] (FP64 scenes)
-    const float2 *g32;   // [nv][nu] (mixed scenes)
+    const float4 *g32;   // [nv][nu - 1] node pairs (g[j][i], g[j][i + 1]) (mixed scenes)
 };
 
 // Scene constants passed by value to every kernel.

@@ -484,15 +484,22 @@ harm_status harm_scene_set_pattern(harm_scene *s, int32_t antenna, int32_t nu, i
             }
             L.g64 = (const double2 *)p;
         } else {
-            std::vector<float2> g32(nn);
-            for (size_t i = 0; i < nn; ++i) g32[i] = make_float2((float)gain_host[2 * i], (float)gain_host[2 * i + 1]);
-            HARM_CUDA(cudaMalloc(&p, nn * sizeof(float2)), "cudaMalloc u-v grid");
-            cudaError_t e = cudaMemcpy(p, g32.data(), nn * sizeof(float2), cudaMemcpyHostToDevice);
+            // each entry holds a node and its right neighbour: a bilinear lookup reads two
+            // 16-byte entries (rows j and j + 1)
+            const size_t np = (size_t)(nu - 1) * nv;
+            std::vector<float4> g32(np);
+            for (int j = 0; j < nv; ++j)
+                for (int i = 0; i + 1 < nu; ++i) {
+                    const double *a = gain_host + 2 * ((size_t)j * nu + i);
+                    g32[(size_t)j * (nu - 1) + i] = make_float4((float)a[0], (float)a[1], (float)a[2], (float)a[3]);
+                }
+            HARM_CUDA(cudaMalloc(&p, np * sizeof(float4)), "cudaMalloc u-v grid");
+            cudaError_t e = cudaMemcpy(p, g32.data(), np * sizeof(float4), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) {
                 cudaFree(p);
                 return cuda_fail(e, "upload u-v grid");
             }
-            L.g32 = (const float2 *)p;
+            L.g32 = (const float4 *)p;
         }
         s->lut_mem[slot] = p;
         s->dev.lut_mask |= 1u << slot;
