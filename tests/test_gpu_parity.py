@@ -116,6 +116,22 @@ def test_ragged_grid_and_unaligned_pulse_window():
         assert rel_rms(got, want) < tol
 
 
+def test_sixteen_channels_maximum():
+    # the channel maximum: Harmony A and B with 8 phase centres each (a 16-channel
+    # scene needs more shared memory per CTA than two CTAs per SM allow)
+    pcs = tuple(5.0 * (i - 3.5) for i in range(8))
+    d = small_wave_scene(n_pulses=40, nx=70, ny=33, n_range=1024)
+    d["tx"], d["rx"] = hs.geometry(40, ("A", "B"), pcs)
+    assert len(d["rx"]) == harm.HARM_MAX_CHANNELS
+    pulses = [0, 17, 39]
+    want = oracle.echo(d, pulses)
+    for prec, tol, dt in ((harm.HARM_PREC_FP64, TOL_FP64, "c128"), (harm.HARM_PREC_MIXED, TOL_MIXED, "c64")):
+        got = run_echo(d, prec, 0, 40, dt)[:, pulses, :]
+        assert rel_rms(got, want) < tol
+        for c in range(16):
+            assert rel_rms(got[c], want[c]) < tol
+
+
 def test_echo_partly_outside_range_window():
     # a short range window cuts the echo: taps outside [0, n_range) are dropped
     d = small_wave_scene(n_pulses=16, nx=64, ny=64, n_range=1024)
