@@ -188,6 +188,22 @@ harm_status harm_facets_generate(harm_scene *scene, int32_t n0, int32_t np, void
 harm_status harm_echo_accumulate(harm_scene *scene, int32_t n0, int32_t np, void *iq_dev,
                                  harm_dtype dtype, int32_t zero_first);
 
+/* Echo into HOST memory (Sec. IV-B: raw data leave the GPU while the next part
+   is computed): writes the IQ of pulses [n0, n0 + np) to iq_host, laid out
+   [n_channels][np][n_range] complex of `dtype` (overwritten, not added to). The
+   burst runs in blocks of block_pulses pulses (<= 0: about an eighth of the
+   burst, a multiple of 128 pulses) into a ring of two device buffers that the
+   scene owns; each block is copied to iq_host on a second stream while the next
+   one is computed. iq_host must be page-locked (cudaHostAlloc / cudaHostRegister)
+   and stay valid until the scene's stream has passed the call: like every call
+   here it is asynchronous, and iq_host is complete after harm_scene_sync (or a
+   wait on the scene's stream). The ring (2 x n_channels x block x n_range
+   elements) is kept for later calls and freed with the scene.
+   Errors: HARM_E_INVALID (window, NULL or pageable iq_host, dtype), HARM_E_OOM
+   (ring allocation), HARM_E_CUDA. */
+harm_status harm_echo_accumulate_host(harm_scene *scene, int32_t n0, int32_t np, void *iq_host,
+                                      harm_dtype dtype, int32_t block_pulses);
+
 /* Adjoint of harm_echo_accumulate with respect to the per-cell NRCS base and the
    per-cell current (the transposed scatter as a gather over range bins): for the
    misfit L = sum |IQ - target|^2 and residual r = IQ - target (resid_dev, same

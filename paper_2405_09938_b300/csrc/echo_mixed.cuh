@@ -58,7 +58,8 @@ constexpr int WA_LO = 14;     // (a 32 x 16 facet tile spans about +-10 bins aro
                               // outside the window are read from global memory)
 constexpr int NBR = 16;       // pulses per chunk of FP64 tile references
 constexpr int NBG = 128;      // pulses per work item (time-Taylor window of the generator)
-constexpr int WCH = 128;      // wave components per shared-memory chunk
+constexpr int WCH = 128;      // wave components per shared-memory chunk (64 for the 8-field CWM)
+__host__ __device__ constexpr int wave_chunk(int nf) { return nf == 3 ? WCH : WCH / 2; }
 constexpr int SROW = 72;      // floats per bin row of the warp buffer (2 halves of 32 + pad)
 constexpr int SHALF = 36;     // float offset of lanes 16..31 in a row
 constexpr int SBINS = 16;     // bins per warp window
@@ -167,7 +168,7 @@ __host__ __device__ inline Layout layout(int nc, bool dup, int nf)
 {
     Layout L;
     int o = 0;
-    const int wbytes = WCH * nf * kOrders * 8;
+    const int wbytes = wave_chunk(nf) * nf * kOrders * 16;  // entries (w.x, w.x, w.y, w.y)
     const int sbytes = NWARP * SBINS * SROW * 4;
     L.w = o;
     L.stage = o;
@@ -187,7 +188,7 @@ __host__ __device__ inline Layout layout(int nc, bool dup, int nf)
 }
 
 struct Smem {
-    float2 *w;       // [WCH][3][kOrders]
+    float4 *w;       // [wave_chunk][nf][kOrders] time-table entries duplicated for pairs
     float2 *tile;    // [kTileBufs][nc][WT]
     AntRec *tx;      // [NBR]          (scalar layout: adjoint)
     AntRec *rx;      // [NBR][nc]
@@ -206,7 +207,7 @@ __device__ __forceinline__ Smem carve(unsigned char *raw, int nc, bool dup, int 
 {
     Layout L = layout(nc, dup, nf);
     Smem s;
-    s.w = reinterpret_cast<float2 *>(raw + L.w);
+    s.w = reinterpret_cast<float4 *>(raw + L.w);
     s.tile = reinterpret_cast<float2 *>(raw + L.tile);
     s.tx = reinterpret_cast<AntRec *>(raw + L.tx);
     s.rx = reinterpret_cast<AntRec *>(raw + L.rx);
@@ -432,14 +433,15 @@ __device__ __forceinline__ float het_weight(const DevScene &S, int cx, int cy, i
 // (weighted per facet by Eq. 2 for a heterogeneous sea state), the time tables
 // staged in shared-memory chunks.
 template <int NF, bool HET, int UNROLL>
-__device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int ix, int iya, int iyb, bool two,
-                              const SetRange &R, float ca[NF][kOrders], float cb[NF][kOrders])
+__device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int ix, int iya, int iyb,
+                              const SetRange &R, float2 C[NF][kOrders])
 {
     const DevScene &S = A.S;
+    constexpr int CH = wave_chunk(NF);
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
-        for (int o = 0; o < kOrders; ++o) ca[f][o] = cb[f][o] = 0.0f;
+        for (int o = 0; o < kOrders; ++o) C[f][o] = make_float2(0.0f, 0.0f);
     const int nw = S.nw;
     const int ixc = min(ix, S.nx - 1), iyac = min(iya, S.ny - 1), iybc = min(iyb, S.ny - 1);
     for (int cy = R.cy0; cy <= R.cy1; ++cy)
@@ -448,57 +450,40 @@ __device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int
             const float wa = HET ? het_weight(S, cx, cy, ixc, iyac) : 1.0f;
             const float wb = HET ? het_weight(S, cx, cy, ixc, iybc) : 1.0f;
             const size_t qw = (size_t)q * nw;
-            for (int m0 = 0; m0 < nw; m0 += WCH) {
-                const int cnt = min(WCH, nw - m0);
+            for (int m0 = 0; m0 < nw; m0 += CH) {
+                const int cnt = min(CH, nw - m0);
                 __syncthreads();
                 const float2 *src = A.wt + (((size_t)batch * S.n_sets + q) * nw + m0) * NF * kOrders;
-                for (int i = threadIdx.x; i < cnt * NF * kOrders; i += NT) sm.w[i] = src[i];
+                for (int i = threadIdx.x; i < cnt * NF * kOrders; i += NT) {
+                    const float2 w = src[i];
+                    sm.w[i] = make_float4(w.x, w.x, w.y, w.y);
+                }
                 __syncthreads();
-                if (wa == 0.0f && (!two || wb == 0.0f)) continue;
+                if (wa == 0.0f && wb == 0.0f) continue;
 #pragma unroll UNROLL
                 for (int m = 0; m < cnt; ++m) {
                     const size_t qm = qw + m0 + m;
-                    float2 e = __ldg(A.ex + qm * S.nx + ixc);
-                    float2 ya = __ldg(A.ey + qm * S.ny + iyac);
-                    float2 yb = __ldg(A.ey + qm * S.ny + iybc);
-                    float qar = e.x * ya.x - e.y * ya.y, qai = e.x * ya.y + e.y * ya.x;
-                    float qbr = e.x * yb.x - e.y * yb.y, qbi = e.x * yb.y + e.y * yb.x;
+                    const float2 e = __ldg(A.ex + qm * S.nx + ixc);
+                    const float2 ya = __ldg(A.ey + qm * S.ny + iyac);
+                    const float2 yb = __ldg(A.ey + qm * S.ny + iybc);
+                    // component phasors of the two facets, (a, b) pairs: Re and -Im
+                    float2 qr = make_float2(e.x * ya.x - e.y * ya.y, e.x * yb.x - e.y * yb.y);
+                    float2 qi = make_float2(-(e.x * ya.y + e.y * ya.x), -(e.x * yb.y + e.y * yb.x));
                     if (HET) {
-                        qar *= wa;
-                        qai *= wa;
-                        qbr *= wb;
-                        qbi *= wb;
+                        qr = mul2(qr, make_float2(wa, wb));
+                        qi = mul2(qi, make_float2(wa, wb));
                     }
-                    const float2 *wm = sm.w + m * NF * kOrders;
-                    if (two) {
+                    const float4 *wm = sm.w + m * NF * kOrders;
 #pragma unroll
-                        for (int f = 0; f < NF; ++f)
+                    for (int f = 0; f < NF; ++f)
 #pragma unroll
-                            for (int o = 0; o < kOrders; ++o) {
-                                float2 w = wm[f * kOrders + o];
-                                ca[f][o] = fmaf(qar, w.x, fmaf(-qai, w.y, ca[f][o]));
-                                cb[f][o] = fmaf(qbr, w.x, fmaf(-qbi, w.y, cb[f][o]));
-                            }
-                    } else {
-#pragma unroll
-                        for (int f = 0; f < NF; ++f)
-#pragma unroll
-                            for (int o = 0; o < kOrders; ++o) {
-                                float2 w = wm[f * kOrders + o];
-                                ca[f][o] = fmaf(qar, w.x, fmaf(-qai, w.y, ca[f][o]));
-                            }
-                    }
+                        for (int o = 0; o < kOrders; ++o) {
+                            const float4 w = wm[f * kOrders + o];
+                            C[f][o] = fma2(qr, make_float2(w.x, w.y), fma2(qi, make_float2(w.z, w.w), C[f][o]));
+                        }
                 }
             }
         }
-}
-
-__device__ __forceinline__ float horner(const float c[kOrders], float t)
-{
-    float r = c[kOrders - 1];
-#pragma unroll
-    for (int o = kOrders - 2; o >= 0; --o) r = fmaf(r, t, c[o]);
-    return r;
 }
 
 // Speckle of facet f in epoch e: Box-Muller on two Philox words (FP32).
@@ -1176,21 +1161,20 @@ __device__ __forceinline__ void stage_luts(const Smem &sm, const DevScene &S)
 // registers for the pulse loop).
 template <int NF, int UNROLL = 1>
 __device__ __forceinline__ void item_coeffs(const Smem &sm, const MixedArgs &A, int batch, int tx0, int ty0, int ty,
-                                            int ix, int iya, int iyb, bool two, float ca[NF][kOrders],
-                                            float cb[NF][kOrders])
+                                            int ix, int iya, int iyb, float2 C[NF][kOrders])
 {
     const DevScene &S = A.S;
     if (!S.static_surface && S.nw > 0) {
         const SetRange R = set_range(S, tx0, tx0 + TX - 1, ty0, ty0 + ty - 1);
         if (S.het_ncx > 0)
-            taylor_coeffs<NF, true, UNROLL>(sm, A, batch, ix, iya, iyb, two, R, ca, cb);
+            taylor_coeffs<NF, true, UNROLL>(sm, A, batch, ix, iya, iyb, R, C);
         else
-            taylor_coeffs<NF, false, UNROLL>(sm, A, batch, ix, iya, iyb, two, R, ca, cb);
+            taylor_coeffs<NF, false, UNROLL>(sm, A, batch, ix, iya, iyb, R, C);
     } else {
 #pragma unroll
         for (int f = 0; f < NF; ++f)
 #pragma unroll
-            for (int o = 0; o < kOrders; ++o) ca[f][o] = cb[f][o] = 0.0f;
+            for (int o = 0; o < kOrders; ++o) C[f][o] = make_float2(0.0f, 0.0f);
     }
 }
 
@@ -1253,8 +1237,8 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
     const int iya = I.ty0 + (two ? 2 * warp : warp), iyb = iya + 1;
     facet_setup(A, ix, iya, jref, ga);
     facet_setup(A, ix, iyb, jref, gb);
-    float ca[NF][kOrders], cb[NF][kOrders];
-    item_coeffs<NF>(sm, A, I.batch, I.tx0, I.ty0, I.ty, ix, iya, iyb, two, ca, cb);
+    float2 C[NF][kOrders];
+    item_coeffs<NF>(sm, A, I.batch, I.tx0, I.ty0, I.ty, ix, iya, two ? iyb : iya, C);
     __syncthreads();
     // the warp buffers share memory with the wave-table chunk: clear them
     for (int i = threadIdx.x; i < NWARP * SBINS * SROW; i += NT) sm.stage[i] = 0.0f;
@@ -1278,11 +1262,6 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
     G.cv = make_float2(ga.cv, gq.cv);
     G.va = ga.valid;
     G.vb = two && gb.valid;
-    float2 C[NF][kOrders];
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-#pragma unroll
-        for (int o = 0; o < kOrders; ++o) C[f][o] = make_float2(ca[f][o], two ? cb[f][o] : ca[f][o]);
     store_coeffs<NF>(sm, C);
     for (int c0 = I.pa; c0 < I.pe; c0 += NBR) {
         const int ce = min(c0 + NBR, I.pe);
@@ -1484,8 +1463,8 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     const int iya = ty0 + 2 * warp, iyb = iya + 1;  // the forward path's facet rows
     facet_setup(A, ix, iya, jref, ga);
     facet_setup(A, ix, iyb, jref, gb);
-    float ca[NF][kOrders], cb[NF][kOrders];
-    item_coeffs<NF>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, true, ca, cb);
+    float2 C[NF][kOrders];
+    item_coeffs<NF>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, C);
     if (Var<V>::LUT) {
         __syncthreads();
         stage_luts(sm, S);
@@ -1499,11 +1478,6 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     G.cv = make_float2(ga.cv, gb.cv);
     G.va = ga.valid;
     G.vb = gb.valid;
-    float2 C[NF][kOrders];
-#pragma unroll
-    for (int f = 0; f < NF; ++f)
-#pragma unroll
-        for (int o = 0; o < kOrders; ++o) C[f][o] = make_float2(ca[f][o], cb[f][o]);
     store_coeffs<NF>(sm, C);
     GatherSink2<InT> sink;
     sink.win = sm.tile;
@@ -1577,21 +1551,24 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     const int ix = tx0 + lane;
     const int iya = ty0 + 2 * warp, iyb = iya + 1;
     const bool va = ix < S.nx && iya < S.ny, vb = ix < S.nx && iyb < S.ny;
-    float ca[NF][kOrders], cb[NF][kOrders];
-    item_coeffs<NF, 4>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, true, ca, cb);
+    float2 C[NF][kOrders];
+    item_coeffs<NF, 1>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, C);
     const int64_t nf = (int64_t)S.nx * S.ny;
     for (int n = pa; n < pe; ++n) {
-        float tau = A.tau[n];
+        const float2 t = dup(A.tau[n]);
         float *o = state + (size_t)(n - n0) * NF * nf;
-        if (va) {
-            int64_t f = (int64_t)iya * S.nx + ix;
+        float2 st[NF];
 #pragma unroll
-            for (int q = 0; q < NF; ++q) o[q * nf + f] = horner(ca[q], tau);
+        for (int q = 0; q < NF; ++q) st[q] = horner2(C[q], t);
+        if (va) {
+            const int64_t f = (int64_t)iya * S.nx + ix;
+#pragma unroll
+            for (int q = 0; q < NF; ++q) o[q * nf + f] = st[q].x;
         }
         if (vb) {
-            int64_t f = (int64_t)iyb * S.nx + ix;
+            const int64_t f = (int64_t)iyb * S.nx + ix;
 #pragma unroll
-            for (int q = 0; q < NF; ++q) o[q * nf + f] = horner(cb[q], tau);
+            for (int q = 0; q < NF; ++q) o[q * nf + f] = st[q].y;
         }
     }
 }

@@ -45,6 +45,11 @@ struct harm_scene {
     std::vector<double> r0;
     int64_t nf = 0;
     int nw = 0;
+    // echo into host memory: copy stream and a ring of two device blocks
+    cudaStream_t copy_stream = nullptr;
+    void *ring[2] = {nullptr, nullptr};
+    size_t ring_bytes = 0;
+    cudaEvent_t ring_ready[2] = {nullptr, nullptr}, ring_free[2] = {nullptr, nullptr};
 };
 
 namespace harm {
@@ -62,6 +67,7 @@ struct WaveSets {
 };
 
 harm_status build_scene_tables(harm_scene *s);
+void release_host_ring(harm_scene *s);  // copy stream, events and ring of harm_echo_accumulate_host
 harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps, const WaveSets &waves);
 
 cudaError_t launch_generate(harm_scene *s, int n0, int np, void *state);

@@ -307,6 +307,7 @@ void free_scene(harm_scene *s)
 {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
+    harm::release_host_ring(s);
     for (void *p : s->allocs) cudaFree(p);
     for (void *p : s->lut_mem)
         if (p) cudaFree(p);

@@ -84,6 +84,7 @@ SIGNATURES = {
                                          C.c_double, C.c_double, C.POINTER(C.c_double)]),
     "harm_facets_generate": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP]),
     "harm_echo_accumulate": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP, C.c_int, C.c_int32]),
+    "harm_echo_accumulate_host": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP, C.c_int, C.c_int32]),
     "harm_echo_adjoint": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP, C.c_int, _VP, _VP]),
     "harm_scene_sync": (C.c_int, [_VP]),
     "harm_batch_create": (C.c_int, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP)]),
@@ -290,6 +291,19 @@ def _dtype_code(t):
 def harm_echo_accumulate(scene: Scene, n0: int, np_: int, iq, zero_first: bool = True):
     _check(load_library().harm_echo_accumulate(scene.handle, n0, np_, _dev_ptr(iq, "iq"),
                                                _dtype_code(iq), 1 if zero_first else 0))
+
+
+def harm_echo_accumulate_host(scene: Scene, n0: int, np_: int, iq_host, block_pulses: int = 0):
+    """Echo of pulses [n0, n0 + np_) written to ``iq_host``, a contiguous pinned CPU
+    tensor [n_channels][np_][n_range] (complex64 or complex128); complete after
+    :func:`harm_scene_sync`."""
+    import torch
+    if not isinstance(iq_host, torch.Tensor) or iq_host.is_cuda:
+        raise HarmError(HARM_E_INVALID, "iq_host must be a CPU tensor")
+    if not iq_host.is_contiguous():
+        raise HarmError(HARM_E_INVALID, "iq_host must be contiguous")
+    _check(load_library().harm_echo_accumulate_host(scene.handle, n0, np_, C.c_void_p(iq_host.data_ptr()),
+                                                    _dtype_code(iq_host), block_pulses))
 
 
 def harm_echo_adjoint(scene: Scene, n0: int, np_: int, resid, grad_sigma0=None, grad_uv=None):

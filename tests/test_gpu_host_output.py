@@ -1,0 +1,108 @@
+"""Echo into host memory (harm_echo_accumulate_host): pulse blocks computed into
+the scene's device ring and copied to a page-locked host array on a second
+stream. Checked against the device-output call on the same scene (same kernels,
+same work items; only the atomic order differs) and against the FP64 oracle on
+sampled pulses, for ragged blocks, an offset window, both output types, a ring
+that grows between calls, and pageable memory (rejected).
+"""
+import numpy as np
+import pytest
+
+import harm_scenes as hs
+import oracle
+from paper_2405_09938_b300 import harm
+from tests.gpu_util import rel_rms, run_echo
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-4
+TOL_SAME_KERNEL = 2e-6  # two runs of the mixed path: FP32 atomic order only
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _scene():
+    return hs.ati_scene(n_pulses=300, nx=40, ny=32, n_range=1024)
+
+
+def _host_echo(scene, d, n0, np_, dtype, block):
+    import torch
+    out = torch.empty((len(d["rx"]), np_, d["n_range"]), dtype=dtype, pin_memory=True)
+    out.fill_(complex(float("nan"), 0.0))  # every element must be written
+    harm.harm_echo_accumulate_host(scene, n0, np_, out, block_pulses=block)
+    harm.harm_scene_sync(scene)
+    return out.numpy().copy()
+
+
+@pytest.mark.parametrize("block", [100, 64, 0])
+def test_host_output_matches_device_output_ragged_blocks(block):
+    import torch
+    d = _scene()
+    n0, np_ = 20, 250
+    sc = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
+    got = _host_echo(sc, d, n0, np_, torch.complex64, block)
+    want = run_echo(d, harm.HARM_PREC_MIXED, n0, np_, dtype="c64", scene=sc)
+    sc.close()
+    assert np.isfinite(got).all()
+    err = rel_rms(got, want)
+    print("block %d: host vs device output rel RMS %.2e" % (block, err))
+    assert err < TOL_SAME_KERNEL
+    for c in range(len(d["rx"])):
+        assert rel_rms(got[c], want[c]) < TOL_SAME_KERNEL
+
+
+def test_host_output_complex128_against_oracle():
+    import torch
+    d = _scene()
+    n0, np_ = 0, 300
+    sc = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
+    got = _host_echo(sc, d, n0, np_, torch.complex128, 0)
+    sc.close()
+    pulses = [0, 127, 128, 255, 256, 299]  # edges of the default 128-pulse blocks and the tail
+    want = oracle.echo(d, pulses)
+    err = rel_rms(got[:, pulses, :], want)
+    print("host output (complex128) vs oracle: rel RMS %.2e" % err)
+    assert err < TOL_MIXED
+
+
+def test_host_output_ring_grows_and_is_reused():
+    import torch
+    d = _scene()
+    sc = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
+    a = _host_echo(sc, d, 10, 40, torch.complex64, 16)     # small ring
+    b = _host_echo(sc, d, 0, 300, torch.complex64, 200)    # grows it
+    c = _host_echo(sc, d, 10, 40, torch.complex64, 16)     # reuses the large ring
+    sc.close()
+    assert rel_rms(a, c) < TOL_SAME_KERNEL
+    assert rel_rms(b[:, 10:50, :], a) < TOL_SAME_KERNEL
+
+
+def test_host_output_rejects_pageable_memory():
+    import torch
+    d = _scene()
+    sc = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
+    out = torch.empty((len(d["rx"]), 8, d["n_range"]), dtype=torch.complex64)  # not pinned
+    with pytest.raises(harm.HarmError) as e:
+        harm.harm_echo_accumulate_host(sc, 0, 8, out)
+    assert e.value.status == harm.HARM_E_INVALID
+    assert "page-locked" in str(e.value)
+    # the scene stays usable
+    pinned = torch.empty_like(out).pin_memory()
+    harm.harm_echo_accumulate_host(sc, 0, 8, pinned)
+    harm.harm_scene_sync(sc)
+    sc.close()
+    assert np.isfinite(pinned.numpy()).all()
+
+
+def test_host_output_fp64_scene():
+    import torch
+    d = hs.small_static()
+    sc = harm.harm_scene_create(d, harm.HARM_PREC_FP64)
+    got = _host_echo(sc, d, 0, 64, torch.complex128, 24)
+    sc.close()
+    want = oracle.echo(d, list(range(64)))
+    assert rel_rms(got, want) < 1e-7
