@@ -58,8 +58,7 @@ constexpr int WA_LO = 14;     // (a 32 x 16 facet tile spans about +-10 bins aro
                               // outside the window are read from global memory)
 constexpr int NBR = 16;       // pulses per chunk of FP64 tile references
 constexpr int NBG = 128;      // pulses per work item (time-Taylor window of the generator)
-constexpr int WCH = 128;      // wave components per shared-memory chunk (64 for the 8-field CWM)
-__host__ __device__ constexpr int wave_chunk(int nf) { return nf == 3 ? WCH : WCH / 2; }
+constexpr int WCH = 128;      // wave components per shared-memory chunk
 constexpr int SROW = 72;      // floats per bin row of the warp buffer (2 halves of 32 + pad)
 constexpr int SHALF = 36;     // float offset of lanes 16..31 in a row
 constexpr int SBINS = 16;     // bins per warp window
@@ -168,7 +167,7 @@ __host__ __device__ inline Layout layout(int nc, bool dup, int nf)
 {
     Layout L;
     int o = 0;
-    const int wbytes = wave_chunk(nf) * nf * kOrders * 16;  // entries (w.x, w.x, w.y, w.y)
+    const int wbytes = WCH * nf * kOrders * 8;
     const int sbytes = NWARP * SBINS * SROW * 4;
     L.w = o;
     L.stage = o;
@@ -188,7 +187,7 @@ __host__ __device__ inline Layout layout(int nc, bool dup, int nf)
 }
 
 struct Smem {
-    float4 *w;       // [wave_chunk][nf][kOrders] time-table entries duplicated for pairs
+    float4 *w;       // [WCH][nf][kOrders / 2] time-table entries, order pairs
     float2 *tile;    // [kTileBufs][nc][WT]
     AntRec *tx;      // [NBR]          (scalar layout: adjoint)
     AntRec *rx;      // [NBR][nc]
@@ -437,11 +436,14 @@ __device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int
                               const SetRange &R, float2 C[NF][kOrders])
 {
     const DevScene &S = A.S;
-    constexpr int CH = wave_chunk(NF);
+    static_assert(kOrders % 2 == 0, "the contraction packs pairs of Taylor orders");
+    constexpr int KP = kOrders / 2;  // order pairs
+    // accumulators packed over order pairs (2p, 2p + 1), one set per facet
+    float2 ca[NF][KP], cb[NF][KP];
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
-        for (int o = 0; o < kOrders; ++o) C[f][o] = make_float2(0.0f, 0.0f);
+        for (int p = 0; p < KP; ++p) ca[f][p] = cb[f][p] = make_float2(0.0f, 0.0f);
     const int nw = S.nw;
     const int ixc = min(ix, S.nx - 1), iyac = min(iya, S.ny - 1), iybc = min(iyb, S.ny - 1);
     for (int cy = R.cy0; cy <= R.cy1; ++cy)
@@ -450,13 +452,15 @@ __device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int
             const float wa = HET ? het_weight(S, cx, cy, ixc, iyac) : 1.0f;
             const float wb = HET ? het_weight(S, cx, cy, ixc, iybc) : 1.0f;
             const size_t qw = (size_t)q * nw;
-            for (int m0 = 0; m0 < nw; m0 += CH) {
-                const int cnt = min(CH, nw - m0);
+            for (int m0 = 0; m0 < nw; m0 += WCH) {
+                const int cnt = min(WCH, nw - m0);
                 __syncthreads();
-                const float2 *src = A.wt + (((size_t)batch * S.n_sets + q) * nw + m0) * NF * kOrders;
-                for (int i = threadIdx.x; i < cnt * NF * kOrders; i += NT) {
-                    const float2 w = src[i];
-                    sm.w[i] = make_float4(w.x, w.x, w.y, w.y);
+                // entry (m, f, p) = (w[2p].re, w[2p+1].re, w[2p].im, w[2p+1].im)
+                const float4 *src = reinterpret_cast<const float4 *>(A.wt) +
+                                    (((size_t)batch * S.n_sets + q) * nw + m0) * NF * KP;
+                for (int i = threadIdx.x; i < cnt * NF * KP; i += NT) {
+                    const float4 w = src[i];
+                    sm.w[i] = make_float4(w.x, w.z, w.y, w.w);
                 }
                 __syncthreads();
                 if (wa == 0.0f && wb == 0.0f) continue;
@@ -466,23 +470,35 @@ __device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int
                     const float2 e = __ldg(A.ex + qm * S.nx + ixc);
                     const float2 ya = __ldg(A.ey + qm * S.ny + iyac);
                     const float2 yb = __ldg(A.ey + qm * S.ny + iybc);
-                    // component phasors of the two facets, (a, b) pairs: Re and -Im
-                    float2 qr = make_float2(e.x * ya.x - e.y * ya.y, e.x * yb.x - e.y * yb.y);
-                    float2 qi = make_float2(-(e.x * ya.y + e.y * ya.x), -(e.x * yb.y + e.y * yb.x));
+                    // component phasors of the two facets: Re and -Im
+                    float qar = e.x * ya.x - e.y * ya.y, qai = -(e.x * ya.y + e.y * ya.x);
+                    float qbr = e.x * yb.x - e.y * yb.y, qbi = -(e.x * yb.y + e.y * yb.x);
                     if (HET) {
-                        qr = mul2(qr, make_float2(wa, wb));
-                        qi = mul2(qi, make_float2(wa, wb));
+                        qar *= wa;
+                        qai *= wa;
+                        qbr *= wb;
+                        qbi *= wb;
                     }
-                    const float4 *wm = sm.w + m * NF * kOrders;
+                    const float2 dar = dup(qar), dai = dup(qai), dbr = dup(qbr), dbi = dup(qbi);
+                    const float4 *wm = sm.w + m * NF * KP;
 #pragma unroll
                     for (int f = 0; f < NF; ++f)
 #pragma unroll
-                        for (int o = 0; o < kOrders; ++o) {
-                            const float4 w = wm[f * kOrders + o];
-                            C[f][o] = fma2(qr, make_float2(w.x, w.y), fma2(qi, make_float2(w.z, w.w), C[f][o]));
+                        for (int p = 0; p < KP; ++p) {
+                            const float4 w = wm[f * KP + p];
+                            const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
+                            ca[f][p] = fma2(dar, wr, fma2(dai, wi, ca[f][p]));
+                            cb[f][p] = fma2(dbr, wr, fma2(dbi, wi, cb[f][p]));
                         }
                 }
             }
+        }
+#pragma unroll
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int p = 0; p < KP; ++p) {
+            C[f][2 * p] = make_float2(ca[f][p].x, cb[f][p].x);
+            C[f][2 * p + 1] = make_float2(ca[f][p].y, cb[f][p].y);
         }
 }
 
@@ -1238,7 +1254,7 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
     facet_setup(A, ix, iya, jref, ga);
     facet_setup(A, ix, iyb, jref, gb);
     float2 C[NF][kOrders];
-    item_coeffs<NF>(sm, A, I.batch, I.tx0, I.ty0, I.ty, ix, iya, two ? iyb : iya, C);
+    item_coeffs<NF, 4>(sm, A, I.batch, I.tx0, I.ty0, I.ty, ix, iya, two ? iyb : iya, C);
     __syncthreads();
     // the warp buffers share memory with the wave-table chunk: clear them
     for (int i = threadIdx.x; i < NWARP * SBINS * SROW; i += NT) sm.stage[i] = 0.0f;
@@ -1464,7 +1480,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     facet_setup(A, ix, iya, jref, ga);
     facet_setup(A, ix, iyb, jref, gb);
     float2 C[NF][kOrders];
-    item_coeffs<NF>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, C);
+    item_coeffs<NF, 4>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, C);
     if (Var<V>::LUT) {
         __syncthreads();
         stage_luts(sm, S);
@@ -1552,7 +1568,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     const int iya = ty0 + 2 * warp, iyb = iya + 1;
     const bool va = ix < S.nx && iya < S.ny, vb = ix < S.nx && iyb < S.ny;
     float2 C[NF][kOrders];
-    item_coeffs<NF, 1>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, C);
+    item_coeffs<NF, 4>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, C);
     const int64_t nf = (int64_t)S.nx * S.ny;
     for (int n = pa; n < pe; ++n) {
         const float2 t = dup(A.tau[n]);
@@ -1673,7 +1689,9 @@ struct MixedLaunch {
                                 float *state)
     {
         const MixedArgs A = make_args(S, M);
-        const int bytes = layout(S.nc, false, Var<V>::NF).total;
+        // the kernel uses only the wave-table chunk: the rest of the SM's shared
+        // memory stays L1 for the wave phasor tables it reads
+        const int bytes = layout(S.nc, false, Var<V>::NF).w + WCH * Var<V>::NF * kOrders * 8;
         cudaError_t e = prep(generate_mixed_kernel<V>, bytes);
         if (e != cudaSuccess) return e;
         return over_batches(S, M, TY, n0, np, [&](int bb, dim3 grid) {
