@@ -129,19 +129,19 @@ ALGO_FLOPS_ACCUMULATOR = 150.0
 ALGO_FLOPS_GENERATOR_PER_FACET_PULSE = 3072.0
 # What the kernel executes per contribution, from the instruction-mix counters on
 # the 512-pulse capture of the headline scene (FFMA2 = 4 flops, FFMA / FMUL2 /
-# FADD2 = 2, FMUL / FADD = 1; per contribution 35.6 FFMA2 + 22.0 FFMA + 11.0 FMUL2
+# FADD2 = 2, FMUL / FADD = 1; per contribution 41.7 FFMA2 + 9.8 FFMA + 11.0 FMUL2
 # + 11.7 FMUL + 9.2 FADD2 + 1.5 FADD): the time-Taylor generator replaces the
 # direct synthesis, so this is far below the algorithmic count.
 EXECUTED_FLOPS_PER_CONTRIBUTION = 240.2
 # All instructions issued per contribution (thread level, same capture).
-INSTR_PER_CONTRIBUTION = 233.8
+INSTR_PER_CONTRIBUTION = 226.8
 # DRAM bytes (read + write) of one headline launch (2048 pulses), from one ncu
 # capture of dram__bytes_read.sum + dram__bytes_write.sum, and the SHA-256 of the
 # kernel sources it was taken on: the figure is reported only while they match.
-TRAFFIC_BYTES = 81603328 + 25733376
+TRAFFIC_BYTES = 81480960 + 41925632
 TRAFFIC_PULSES = 2048
 TRAFFIC_SOURCES = ("echo_mixed.cuh", "harm_kernels.cuh", "harm_internal.cuh")
-TRAFFIC_SHA256 = "7e69e0f17fb26be3828142de74c6a38ce31ea709f468be4b42624cda0843a7cb"
+TRAFFIC_SHA256 = "034735c79af8292533917664025c3a002392882acd5cf46db36904d428dc7cf7"
 
 
 def captured_traffic(np_step):
@@ -566,17 +566,18 @@ def _launches_per_step(desc, prec, np_step):
 
 
 def _scene_table_bytes(desc, prec):
-    """Bytes harm_scene_create uploads: pulse and receive states, wave tables,
-    u-v grid descriptors and the flag words."""
+    """Bytes harm_scene_create uploads: pulse and receive states, the wave list
+    (its phasor tables are computed on the device), the Taylor time tables, u-v
+    grid descriptors and the flag words."""
     from paper_2405_09938_b300 import harm
     nw = desc["n_omega"] * desc["n_theta"]
-    npul, nc, nx, ny = desc["n_pulses"], len(desc["rx"]), desc["nx"], desc["ny"]
+    npul, nc = desc["n_pulses"], len(desc["rx"])
     pulse = npul * (8 * 2 + 8 * 10) + npul * nc * (8 * 10 + 16)
     if prec == harm.HARM_PREC_MIXED:
         nf = 8 if desc.get("cwm") else 3
-        waves = nw * (nx + ny) * 8 + math.ceil(npul / 128) * nw * nf * 6 * 8 + npul * 4 + nw * 32
+        waves = nw * 40 + math.ceil(npul / 128) * nw * nf * 6 * 8 + npul * 4 + nw * 32
     else:
-        waves = nw * (nx + ny + npul) * 16 + nw * 32
+        waves = nw * 40 + nw * 32
     return pulse + waves + (1 + nc) * 56 + 16
 
 

@@ -1,6 +1,7 @@
 // Launch dispatch by precision, and the host-side tables of the mixed path:
 // FP32 separable wave phasors, Taylor-in-time tables per pulse batch, and the
 // Kaiser-sinc tap polynomials.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -12,6 +13,65 @@ namespace harm {
 int mixed_batch_pulses();
 
 namespace {
+
+// One wave component as the table kernel reads it.
+struct WaveDev {
+    double kx, ky, om, amp, ph;
+};
+
+template <typename T2>
+__device__ __forceinline__ T2 make_pair(double a, double b);
+template <>
+__device__ __forceinline__ float2 make_pair<float2>(double a, double b)
+{
+    return make_float2((float)a, (float)b);
+}
+template <>
+__device__ __forceinline__ double2 make_pair<double2>(double a, double b)
+{
+    return make_double2(a, b);
+}
+
+// Separable phasor tables of the linear surface (Sec. III: each component is a
+// plane wave, so its phase k.x - omega t + phi splits into an x, a y and a time
+// factor), evaluated in FP64 and stored as T2: ex[qm][ix] = e^{i kx x},
+// ey[qm][iy] = a e^{i (ky y + phi)} and, when tt is given, tt[qm][n] =
+// e^{-i omega t_s(n)}; qm runs over every component of every wave set.
+template <typename T2>
+__global__ void phasor_tables_kernel(const WaveDev *waves, int nsw, int nx, int ny, int np, double dx,
+                                     const PulseState *ps, T2 *ex, T2 *ey, T2 *tt)
+{
+    const int per = nx + ny + (tt ? np : 0);
+    const size_t total = (size_t)nsw * per;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int qm = (int)(i / per), j = (int)(i % per);
+        const WaveDev w = waves[qm];
+        double sn, cs;
+        if (j < nx) {
+            sincos(w.kx * ((j + 0.5 - 0.5 * nx) * dx), &sn, &cs);
+            ex[(size_t)qm * nx + j] = make_pair<T2>(cs, sn);
+        } else if (j < nx + ny) {
+            const int iy = j - nx;
+            sincos(w.ky * ((iy + 0.5 - 0.5 * ny) * dx) + w.ph, &sn, &cs);
+            ey[(size_t)qm * ny + iy] = make_pair<T2>(w.amp * cs, w.amp * sn);
+        } else {
+            const int n = j - nx - ny;
+            sincos(-w.om * ps[n].ts, &sn, &cs);
+            tt[(size_t)qm * np + n] = make_pair<T2>(cs, sn);
+        }
+    }
+}
+
+template <typename T>
+cudaError_t dev_alloc(harm_scene *s, size_t count, T **out)
+{
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    s->allocs.push_back(p);
+    *out = (T *)p;
+    return cudaSuccess;
+}
 
 template <typename T>
 cudaError_t upload_raw(harm_scene *s, const std::vector<T> &h, const T **out)
@@ -110,6 +170,41 @@ void fit_sinc2(float out[kSincDeg + 1])
 
 }  // namespace
 
+template <typename T2>
+cudaError_t phasor_tables(harm_scene *s, const WaveSets &W, const PulseState *ps_dev, const T2 **ex,
+                          const T2 **ey, const T2 **tt)
+{
+    const harm_scene_desc &d = s->desc;
+    const int nx = d.nx, ny = d.ny, np = d.n_pulses;
+    const int nsw = W.n_sets * std::max(W.nw, 1);
+    std::vector<WaveDev> h((size_t)nsw, WaveDev{0.0, 0.0, 0.0, 0.0, 0.0});
+    for (int q = 0; q < W.n_sets; ++q)
+        for (int m = 0; m < W.nw; ++m) {
+            const Wave &w = W.at(q, m);
+            h[(size_t)q * W.nw + m] = WaveDev{w.kx, w.ky, w.om, w.amp, w.ph};
+        }
+    const WaveDev *wd = nullptr;
+    T2 *pex = nullptr, *pey = nullptr, *ptt = nullptr;
+    cudaError_t e = upload_raw(s, h, &wd);
+    if (e == cudaSuccess) e = dev_alloc(s, (size_t)nsw * nx, &pex);
+    if (e == cudaSuccess) e = dev_alloc(s, (size_t)nsw * ny, &pey);
+    if (e == cudaSuccess && tt) e = dev_alloc(s, (size_t)nsw * np, &ptt);
+    if (e != cudaSuccess) return e;
+    const size_t total = (size_t)nsw * (nx + ny + (tt ? np : 0));
+    const int threads = 256;
+    const int blocks = (int)std::min<size_t>((total + threads - 1) / threads, 148 * 16);
+    phasor_tables_kernel<T2><<<blocks, threads, 0, s->stream>>>(wd, nsw, nx, ny, np, d.facet_m, ps_dev, pex, pey,
+                                                                ptt);
+    e = cudaGetLastError();
+    *ex = pex;
+    *ey = pey;
+    if (tt) *tt = ptt;
+    return e;
+}
+
+template cudaError_t phasor_tables<double2>(harm_scene *, const WaveSets &, const PulseState *, const double2 **,
+                                            const double2 **, const double2 **);
+
 harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps, const WaveSets &W)
 {
     const harm_scene_desc &d = s->desc;
@@ -121,20 +216,6 @@ harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps,
     M.n_batches = (np + M.nb - 1) / M.nb;
     M.nf = nf;
     const size_t nsw = (size_t)nsets * std::max(nw, 1);
-    std::vector<float2> ex(nsw * nx), ey(nsw * ny);
-    for (int q = 0; q < nsets; ++q)
-        for (int m = 0; m < nw; ++m) {
-            const Wave &w = W.at(q, m);
-            const size_t qm = (size_t)q * nw + m;
-            for (int ix = 0; ix < nx; ++ix) {
-                double a = w.kx * (ix + 0.5 - 0.5 * nx) * d.facet_m;
-                ex[qm * nx + ix] = make_float2((float)std::cos(a), (float)std::sin(a));
-            }
-            for (int iy = 0; iy < ny; ++iy) {
-                double a = w.ky * (iy + 0.5 - 0.5 * ny) * d.facet_m + w.ph;
-                ey[qm * ny + iy] = make_float2((float)(w.amp * std::cos(a)), (float)(w.amp * std::sin(a)));
-            }
-        }
     // Taylor tables: E_{w,o} = e^{-i omega t_c} (-i omega)^o / o! about the batch
     // centre t_c, times the complex factor c_f of each field (state field f =
     // Re(c_f Q E) for the component phasor Q): eta (1), eta_x (i kx), eta_y (i ky),
@@ -172,7 +253,7 @@ harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps,
     }
     fit_taps(s->dev, M.tap);
     fit_sinc2(M.sinc2);
-    if (upload_raw(s, ex, &M.ex) != cudaSuccess || upload_raw(s, ey, &M.ey) != cudaSuccess ||
+    if (phasor_tables<float2>(s, W, nullptr, &M.ex, &M.ey, nullptr) != cudaSuccess ||
         upload_raw(s, wt, &M.wt) != cudaSuccess || upload_raw(s, tau, &M.tau) != cudaSuccess)
         return HARM_E_CUDA;
     return HARM_OK;

@@ -69,6 +69,12 @@ struct WaveSets {
 harm_status build_scene_tables(harm_scene *s);
 void release_host_ring(harm_scene *s);  // copy stream, events and ring of harm_echo_accumulate_host
 harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps, const WaveSets &waves);
+// Separable phasor tables of every wave set, computed on the device in FP64 and
+// stored as T2 (float2 or double2) on the scene's stream; tt (FP64 path only,
+// e^{-i omega t_s(n)} per pulse) needs the uploaded pulse states ps_dev.
+template <typename T2>
+cudaError_t phasor_tables(harm_scene *s, const WaveSets &W, const PulseState *ps_dev, const T2 **ex, const T2 **ey,
+                          const T2 **tt);
 
 cudaError_t launch_generate(harm_scene *s, int n0, int np, void *state);
 cudaError_t launch_accumulate(harm_scene *s, int n0, int np, void *iq, harm_dtype dtype);

@@ -682,8 +682,9 @@ harm_status build_scene_tables(harm_scene *s)
             r.p_ref = (rsum - s->r0[c]) / dr;
         }
 
-    // waves: separable phasor tables e^{i kx x}, a e^{i phi} e^{i ky y}, e^{-i omega t_s}
-    // for every wave set
+    // waves: wave numbers and frequencies of every wave set here; their separable
+    // phasor tables e^{i kx x}, a e^{i phi} e^{i ky y} (and e^{-i omega t_s} for the
+    // FP64 path) are evaluated on the device by phasor_tables
     const WaveSets W = wave_sets(s);
     const int nw = W.nw, nsets = W.n_sets;
     s->nw = nw;
@@ -691,12 +692,6 @@ harm_status build_scene_tables(harm_scene *s)
     v.n_sets = nsets;
     std::vector<double> kx((size_t)nsets * nw), ky((size_t)nsets * nw), om((size_t)nsets * nw),
         kn((size_t)nsets * nw);
-    std::vector<double2> ex, ey, tt;
-    if (d.precision == HARM_PREC_FP64) {
-        ex.resize((size_t)nsets * nw * nx);
-        ey.resize((size_t)nsets * nw * ny);
-        tt.resize((size_t)nsets * nw * np);
-    }
     for (int q = 0; q < nsets; ++q)
         for (int m = 0; m < nw; ++m) {
             const Wave &w = W.at(q, m);
@@ -705,21 +700,6 @@ harm_status build_scene_tables(harm_scene *s)
             ky[qm] = w.ky;
             om[qm] = w.om;
             kn[qm] = std::sqrt(w.kx * w.kx + w.ky * w.ky);
-            if (d.precision != HARM_PREC_FP64) continue;
-            for (int ix = 0; ix < nx; ++ix) {
-                double x = (ix + 0.5 - 0.5 * nx) * d.facet_m;
-                double a = w.kx * x;
-                ex[qm * nx + ix] = make_double2(std::cos(a), std::sin(a));
-            }
-            for (int iy = 0; iy < ny; ++iy) {
-                double y = (iy + 0.5 - 0.5 * ny) * d.facet_m;
-                double a = w.ky * y + w.ph;
-                ey[qm * ny + iy] = make_double2(w.amp * std::cos(a), w.amp * std::sin(a));
-            }
-            for (int n = 0; n < np; ++n) {
-                double a = -w.om * ps[n].ts;
-                tt[qm * np + n] = make_double2(std::cos(a), std::sin(a));
-            }
         }
 
     harm_status st;
@@ -738,11 +718,8 @@ harm_status build_scene_tables(harm_scene *s)
         s->luts_dev = const_cast<PatLut *>(lp);
         v.luts = lp;
     }
-    if (d.precision == HARM_PREC_FP64) {
-        if ((st = upload(s, ex, &v.ex)) != HARM_OK) return st;
-        if ((st = upload(s, ey, &v.ey)) != HARM_OK) return st;
-        if ((st = upload(s, tt, &v.tt)) != HARM_OK) return st;
-    }
+    if (d.precision == HARM_PREC_FP64)
+        HARM_CUDA(phasor_tables<double2>(s, W, v.pulses, &v.ex, &v.ey, &v.tt), "wave phasor tables");
     std::vector<unsigned int> flags(4, 0u);
     const unsigned int *fl = nullptr;
     if ((st = upload(s, flags, &fl)) != HARM_OK) return st;
