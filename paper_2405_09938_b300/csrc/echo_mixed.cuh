@@ -866,6 +866,17 @@ struct GatherSink2 {
     }
 };
 
+// Pin a per-item value (derived once from FP64 scene constants) in a register:
+// the empty asm hides how it was computed, so under register pressure the
+// compiler keeps or spills it instead of recomputing it, with FP64 multiplies
+// and conversions, inside the pulse loop.
+__device__ __forceinline__ float pin(float v)
+{
+    asm volatile("" : "+f"(v));
+    return v;
+}
+__device__ __forceinline__ float2 pin(float2 v) { return make_float2(pin(v.x), pin(v.y)); }
+
 // Per-thread pair of facets (same column, adjacent rows) for the packed path.
 struct PairGeo {
     float2 xi_y, fj, base_area, amp_static, cu, cv, zr, zi;
@@ -1243,8 +1254,8 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
     const int iref = I.tx0 + TX / 2, jref = I.ty0 + I.ty / 2;
     const double xr = (iref + 0.5 - 0.5 * S.nx) * S.dx;
     const double yr = (jref + 0.5 - 0.5 * S.ny) * S.dx;
-    const float xi_x = (float)((ix - iref) * S.dx);
-    const float fi = (float)(ix - iref);
+    const float xi_x = pin((float)((ix - iref) * S.dx));
+    const float fi = pin((float)(ix - iref));
 
     FacetGeo ga, gb;
     // rows of the thread's two facets: adjacent rows 2w, 2w + 1 (16-row tiles; their
@@ -1270,12 +1281,12 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
     // pack the two facets: .x = row w, .y = row w + 8 (a copy of .x, masked off, for 8-row tiles)
     PairGeo G;
     const FacetGeo &gq = two ? gb : ga;
-    G.xi_y = make_float2(ga.xi_y, gq.xi_y);
-    G.fj = make_float2(ga.fj, gq.fj);
-    G.base_area = make_float2(ga.base_area, gq.base_area);
-    G.amp_static = make_float2(ga.amp_static, gq.amp_static);
-    G.cu = make_float2(ga.cu, gq.cu);
-    G.cv = make_float2(ga.cv, gq.cv);
+    G.xi_y = pin(make_float2(ga.xi_y, gq.xi_y));
+    G.fj = pin(make_float2(ga.fj, gq.fj));
+    G.base_area = pin(make_float2(ga.base_area, gq.base_area));
+    G.amp_static = pin(make_float2(ga.amp_static, gq.amp_static));
+    G.cu = pin(make_float2(ga.cu, gq.cu));
+    G.cv = pin(make_float2(ga.cv, gq.cv));
     G.va = ga.valid;
     G.vb = two && gb.valid;
     store_coeffs<NF>(sm, C);
@@ -1472,8 +1483,8 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     const int iref = tx0 + TX / 2, jref = ty0 + TY / 2;
     const double xr = (iref + 0.5 - 0.5 * S.nx) * S.dx;
     const double yr = (jref + 0.5 - 0.5 * S.ny) * S.dx;
-    const float xi_x = (float)((ix - iref) * S.dx);
-    const float fi = (float)(ix - iref);
+    const float xi_x = pin((float)((ix - iref) * S.dx));
+    const float fi = pin((float)(ix - iref));
 
     FacetGeo ga, gb;
     const int iya = ty0 + 2 * warp, iyb = iya + 1;  // the forward path's facet rows
@@ -1486,12 +1497,12 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
         stage_luts(sm, S);
     }
     PairGeo G;
-    G.xi_y = make_float2(ga.xi_y, gb.xi_y);
-    G.fj = make_float2(ga.fj, gb.fj);
-    G.base_area = make_float2(ga.base_area, gb.base_area);
-    G.amp_static = make_float2(ga.amp_static, gb.amp_static);
-    G.cu = make_float2(ga.cu, gb.cu);
-    G.cv = make_float2(ga.cv, gb.cv);
+    G.xi_y = pin(make_float2(ga.xi_y, gb.xi_y));
+    G.fj = pin(make_float2(ga.fj, gb.fj));
+    G.base_area = pin(make_float2(ga.base_area, gb.base_area));
+    G.amp_static = pin(make_float2(ga.amp_static, gb.amp_static));
+    G.cu = pin(make_float2(ga.cu, gb.cu));
+    G.cv = pin(make_float2(ga.cv, gb.cv));
     G.va = ga.valid;
     G.vb = gb.valid;
     store_coeffs<NF>(sm, C);
