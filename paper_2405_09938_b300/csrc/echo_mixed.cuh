@@ -58,7 +58,7 @@ constexpr int WA_LO = 14;     // (a 32 x 16 facet tile spans about +-10 bins aro
                               // outside the window are read from global memory)
 constexpr int NBR = 16;       // pulses per chunk of FP64 tile references
 constexpr int NBG = 128;      // pulses per work item (time-Taylor window of the generator)
-constexpr int WCH = 128;      // wave components per shared-memory chunk
+constexpr int WCH = 64;       // wave components per shared-memory chunk of the generator
 constexpr int SROW = 72;      // floats per bin row of the warp buffer (2 halves of 32 + pad)
 constexpr int SHALF = 36;     // float offset of lanes 16..31 in a row
 constexpr int SBINS = 16;     // bins per warp window
@@ -152,6 +152,10 @@ struct PolyArgs {
     float2 sinc2[kSincDeg + 1];
 };
 
+// Bytes of one generator chunk in shared memory: the time tables of WCH wave
+// components (order pairs) and their phasors on the tile's columns and rows.
+__host__ __device__ constexpr int wave_chunk_bytes(int nf) { return WCH * (nf * (kOrders / 2) * 16 + (TX + TY) * 8); }
+
 // Shared-memory layout (bytes), sized for nc channels and nf state fields.
 struct Layout {
     int w, tile, tx, rx, ch, pr, txd, stage, lut, coef, total;
@@ -167,7 +171,7 @@ __host__ __device__ inline Layout layout(int nc, bool dup, int nf)
 {
     Layout L;
     int o = 0;
-    const int wbytes = WCH * nf * kOrders * 8;
+    const int wbytes = wave_chunk_bytes(nf);
     const int sbytes = NWARP * SBINS * SROW * 4;
     L.w = o;
     L.stage = o;
@@ -188,6 +192,8 @@ __host__ __device__ inline Layout layout(int nc, bool dup, int nf)
 
 struct Smem {
     float4 *w;       // [WCH][nf][kOrders / 2] time-table entries, order pairs
+    float2 *wx;      // [WCH][TX] e^{i kx x} of the tile's columns
+    float2 *wy;      // [WCH][TY] a e^{i (ky y + phi)} of the tile's rows
     float2 *tile;    // [kTileBufs][nc][WT]
     AntRec *tx;      // [NBR]          (scalar layout: adjoint)
     AntRec *rx;      // [NBR][nc]
@@ -207,6 +213,8 @@ __device__ __forceinline__ Smem carve(unsigned char *raw, int nc, bool dup, int 
     Layout L = layout(nc, dup, nf);
     Smem s;
     s.w = reinterpret_cast<float4 *>(raw + L.w);
+    s.wx = reinterpret_cast<float2 *>(raw + L.w + WCH * nf * (kOrders / 2) * 16);
+    s.wy = s.wx + WCH * TX;
     s.tile = reinterpret_cast<float2 *>(raw + L.tile);
     s.tx = reinterpret_cast<AntRec *>(raw + L.tx);
     s.rx = reinterpret_cast<AntRec *>(raw + L.rx);
@@ -432,8 +440,8 @@ __device__ __forceinline__ float het_weight(const DevScene &S, int cx, int cy, i
 // (weighted per facet by Eq. 2 for a heterogeneous sea state), the time tables
 // staged in shared-memory chunks.
 template <int NF, bool HET, int UNROLL>
-__device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int ix, int iya, int iyb,
-                              const SetRange &R, float2 C[NF][kOrders])
+__device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int tx0, int ty0, int ix, int iya,
+                              int iyb, const SetRange &R, float2 C[NF][kOrders])
 {
     const DevScene &S = A.S;
     static_assert(kOrders % 2 == 0, "the contraction packs pairs of Taylor orders");
@@ -446,6 +454,8 @@ __device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int
         for (int p = 0; p < KP; ++p) ca[f][p] = cb[f][p] = make_float2(0.0f, 0.0f);
     const int nw = S.nw;
     const int ixc = min(ix, S.nx - 1), iyac = min(iya, S.ny - 1), iybc = min(iyb, S.ny - 1);
+    // the thread's column and rows within the staged tile phasors
+    const int cx_s = ixc - tx0, ra_s = iyac - ty0, rb_s = iybc - ty0;
     for (int cy = R.cy0; cy <= R.cy1; ++cy)
         for (int cx = R.cx0; cx <= R.cx1; ++cx) {
             const int q = HET ? cy * S.het_ncx + cx : 0;
@@ -462,14 +472,23 @@ __device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int
                     const float4 w = src[i];
                     sm.w[i] = make_float4(w.x, w.z, w.y, w.w);
                 }
+                // phasors of the chunk's components on the tile's columns and rows
+                // (clamped to the scene at its edges)
+                for (int i = threadIdx.x; i < cnt * TX; i += NT) {
+                    const int m = i / TX, c = min(tx0 + i % TX, S.nx - 1);
+                    sm.wx[i] = __ldg(A.ex + (qw + m0 + m) * S.nx + c);
+                }
+                for (int i = threadIdx.x; i < cnt * TY; i += NT) {
+                    const int m = i / TY, r = min(ty0 + i % TY, S.ny - 1);
+                    sm.wy[i] = __ldg(A.ey + (qw + m0 + m) * S.ny + r);
+                }
                 __syncthreads();
                 if (wa == 0.0f && wb == 0.0f) continue;
 #pragma unroll UNROLL
                 for (int m = 0; m < cnt; ++m) {
-                    const size_t qm = qw + m0 + m;
-                    const float2 e = __ldg(A.ex + qm * S.nx + ixc);
-                    const float2 ya = __ldg(A.ey + qm * S.ny + iyac);
-                    const float2 yb = __ldg(A.ey + qm * S.ny + iybc);
+                    const float2 e = sm.wx[m * TX + cx_s];
+                    const float2 ya = sm.wy[m * TY + ra_s];
+                    const float2 yb = sm.wy[m * TY + rb_s];
                     // component phasors of the two facets: Re and -Im
                     float qar = e.x * ya.x - e.y * ya.y, qai = -(e.x * ya.y + e.y * ya.x);
                     float qbr = e.x * yb.x - e.y * yb.y, qbi = -(e.x * yb.y + e.y * yb.x);
@@ -1183,9 +1202,9 @@ __device__ __forceinline__ void stage_luts(const Smem &sm, const DevScene &S)
 }
 
 // Taylor coefficients of the item's two facets per thread, or zero for a static
-// surface. UNROLL unrolls the component loop (the standalone generator, which does
-// little else, hides the table loads that way; the echo kernels keep their
-// registers for the pulse loop).
+// surface. UNROLL unrolls the component loop to overlap the shared-memory reads of
+// consecutive components (measured best: 4 in the echo kernels, 8 in the
+// standalone generator, which has no pulse loop competing for registers).
 template <int NF, int UNROLL = 1>
 __device__ __forceinline__ void item_coeffs(const Smem &sm, const MixedArgs &A, int batch, int tx0, int ty0, int ty,
                                             int ix, int iya, int iyb, float2 C[NF][kOrders])
@@ -1194,9 +1213,9 @@ __device__ __forceinline__ void item_coeffs(const Smem &sm, const MixedArgs &A, 
     if (!S.static_surface && S.nw > 0) {
         const SetRange R = set_range(S, tx0, tx0 + TX - 1, ty0, ty0 + ty - 1);
         if (S.het_ncx > 0)
-            taylor_coeffs<NF, true, UNROLL>(sm, A, batch, ix, iya, iyb, R, C);
+            taylor_coeffs<NF, true, UNROLL>(sm, A, batch, tx0, ty0, ix, iya, iyb, R, C);
         else
-            taylor_coeffs<NF, false, UNROLL>(sm, A, batch, ix, iya, iyb, R, C);
+            taylor_coeffs<NF, false, UNROLL>(sm, A, batch, tx0, ty0, ix, iya, iyb, R, C);
     } else {
 #pragma unroll
         for (int f = 0; f < NF; ++f)
@@ -1579,7 +1598,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     const int iya = ty0 + 2 * warp, iyb = iya + 1;
     const bool va = ix < S.nx && iya < S.ny, vb = ix < S.nx && iyb < S.ny;
     float2 C[NF][kOrders];
-    item_coeffs<NF, 4>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, C);
+    item_coeffs<NF, 8>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, C);
     const int64_t nf = (int64_t)S.nx * S.ny;
     for (int n = pa; n < pe; ++n) {
         const float2 t = dup(A.tau[n]);
@@ -1702,7 +1721,7 @@ struct MixedLaunch {
         const MixedArgs A = make_args(S, M);
         // the kernel uses only the wave-table chunk: the rest of the SM's shared
         // memory stays L1 for the wave phasor tables it reads
-        const int bytes = layout(S.nc, false, Var<V>::NF).w + WCH * Var<V>::NF * kOrders * 8;
+        const int bytes = layout(S.nc, false, Var<V>::NF).w + wave_chunk_bytes(Var<V>::NF);
         cudaError_t e = prep(generate_mixed_kernel<V>, bytes);
         if (e != cudaSuccess) return e;
         return over_batches(S, M, TY, n0, np, [&](int bb, dim3 grid) {
