@@ -127,7 +127,8 @@ struct PatLutF {
 
 struct MixedArgs {
     DevScene S;
-    const float2 *ex, *ey, *wt;
+    const float2 *ex, *ey, *tc;
+    const float *cr;
     const float *tau;
     int nb, n_batches;
     // FP32 constants
@@ -154,7 +155,7 @@ struct PolyArgs {
 
 // Bytes of one generator chunk in shared memory: the time tables of WCH wave
 // components (order pairs) and their phasors on the tile's columns and rows.
-__host__ __device__ constexpr int wave_chunk_bytes(int nf) { return WCH * (nf * (kOrders / 2) * 16 + (TX + TY) * 8); }
+__host__ __device__ constexpr int wave_chunk_bytes(int nf) { return WCH * (nf * kOrders * 4 + (TX + TY) * 8); }
 
 // Shared-memory layout (bytes), sized for nc channels and nf state fields.
 struct Layout {
@@ -191,7 +192,7 @@ __host__ __device__ inline Layout layout(int nc, bool dup, int nf)
 }
 
 struct Smem {
-    float4 *w;       // [WCH][nf][kOrders / 2] time-table entries, order pairs
+    float2 *w;       // [WCH][nf][kOrders / 2] real Taylor factors, order pairs (2p, 2p + 1)
     float2 *wx;      // [WCH][TX] e^{i kx x} of the tile's columns
     float2 *wy;      // [WCH][TY] a e^{i (ky y + phi)} of the tile's rows
     float2 *tile;    // [kTileBufs][nc][WT]
@@ -212,8 +213,8 @@ __device__ __forceinline__ Smem carve(unsigned char *raw, int nc, bool dup, int 
 {
     Layout L = layout(nc, dup, nf);
     Smem s;
-    s.w = reinterpret_cast<float4 *>(raw + L.w);
-    s.wx = reinterpret_cast<float2 *>(raw + L.w + WCH * nf * (kOrders / 2) * 16);
+    s.w = reinterpret_cast<float2 *>(raw + L.w);
+    s.wx = reinterpret_cast<float2 *>(raw + L.w + WCH * nf * kOrders * 4);
     s.wy = s.wx + WCH * TX;
     s.tile = reinterpret_cast<float2 *>(raw + L.tile);
     s.tx = reinterpret_cast<AntRec *>(raw + L.tx);
@@ -465,22 +466,20 @@ __device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int
             for (int m0 = 0; m0 < nw; m0 += WCH) {
                 const int cnt = min(WCH, nw - m0);
                 __syncthreads();
-                // entry (m, f, p) = (w[2p].re, w[2p+1].re, w[2p].im, w[2p+1].im)
-                const float4 *src = reinterpret_cast<const float4 *>(A.wt) +
-                                    (((size_t)batch * S.n_sets + q) * nw + m0) * NF * KP;
-                for (int i = threadIdx.x; i < cnt * NF * KP; i += NT) {
-                    const float4 w = src[i];
-                    sm.w[i] = make_float4(w.x, w.z, w.y, w.w);
-                }
+                // real Taylor factors of the chunk, as order pairs
+                const float2 *src = reinterpret_cast<const float2 *>(A.cr) + (qw + m0) * NF * KP;
+                for (int i = threadIdx.x; i < cnt * NF * KP; i += NT) sm.w[i] = src[i];
                 // phasors of the chunk's components on the tile's columns and rows
-                // (clamped to the scene at its edges)
+                // (clamped to the scene at its edges); the rows carry e^{-i omega t_c}
+                const float2 *tcb = A.tc + ((size_t)batch * S.n_sets + q) * nw + m0;
                 for (int i = threadIdx.x; i < cnt * TX; i += NT) {
                     const int m = i / TX, c = min(tx0 + i % TX, S.nx - 1);
                     sm.wx[i] = __ldg(A.ex + (qw + m0 + m) * S.nx + c);
                 }
                 for (int i = threadIdx.x; i < cnt * TY; i += NT) {
                     const int m = i / TY, r = min(ty0 + i % TY, S.ny - 1);
-                    sm.wy[i] = __ldg(A.ey + (qw + m0 + m) * S.ny + r);
+                    const float2 y = __ldg(A.ey + (qw + m0 + m) * S.ny + r), t = __ldg(tcb + m);
+                    sm.wy[i] = make_float2(y.x * t.x - y.y * t.y, y.x * t.y + y.y * t.x);
                 }
                 __syncthreads();
                 if (wa == 0.0f && wb == 0.0f) continue;
@@ -489,26 +488,25 @@ __device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int
                     const float2 e = sm.wx[m * TX + cx_s];
                     const float2 ya = sm.wy[m * TY + ra_s];
                     const float2 yb = sm.wy[m * TY + rb_s];
-                    // component phasors of the two facets: Re and -Im
-                    float qar = e.x * ya.x - e.y * ya.y, qai = -(e.x * ya.y + e.y * ya.x);
-                    float qbr = e.x * yb.x - e.y * yb.y, qbi = -(e.x * yb.y + e.y * yb.x);
+                    // Q of the two facets (and with its parts swapped)
+                    float2 qa = make_float2(e.x * ya.x - e.y * ya.y, e.x * ya.y + e.y * ya.x);
+                    float2 qb = make_float2(e.x * yb.x - e.y * yb.y, e.x * yb.y + e.y * yb.x);
                     if (HET) {
-                        qar *= wa;
-                        qai *= wa;
-                        qbr *= wb;
-                        qbi *= wb;
+                        qa = mul2(qa, dup(wa));
+                        qb = mul2(qb, dup(wb));
                     }
-                    const float2 dar = dup(qar), dai = dup(qai), dbr = dup(qbr), dbi = dup(qbi);
-                    const float4 *wm = sm.w + m * NF * KP;
+                    const float2 sa = make_float2(qa.y, qa.x), sb = make_float2(qb.y, qb.x);
+                    const float2 *wm = sm.w + m * NF * KP;
 #pragma unroll
-                    for (int f = 0; f < NF; ++f)
+                    for (int f = 0; f < NF; ++f) {
+                        const bool real = f == 0 || f >= 5;  // c_f real: (Q_r, Q_i), else (Q_i, Q_r)
 #pragma unroll
                         for (int p = 0; p < KP; ++p) {
-                            const float4 w = wm[f * KP + p];
-                            const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
-                            ca[f][p] = fma2(dar, wr, fma2(dai, wi, ca[f][p]));
-                            cb[f][p] = fma2(dbr, wr, fma2(dbi, wi, cb[f][p]));
+                            const float2 w = wm[f * KP + p];
+                            ca[f][p] = fma2(w, real ? qa : sa, ca[f][p]);
+                            cb[f][p] = fma2(w, real ? qb : sb, cb[f][p]);
                         }
+                    }
                 }
             }
         }
@@ -1203,8 +1201,8 @@ __device__ __forceinline__ void stage_luts(const Smem &sm, const DevScene &S)
 
 // Taylor coefficients of the item's two facets per thread, or zero for a static
 // surface. UNROLL unrolls the component loop to overlap the shared-memory reads of
-// consecutive components (measured best: 4 in the echo kernels, 8 in the
-// standalone generator, which has no pulse loop competing for registers).
+// consecutive components (measured best: 4, in the echo kernels and in the
+// standalone generator at three CTAs per SM).
 template <int NF, int UNROLL = 1>
 __device__ __forceinline__ void item_coeffs(const Smem &sm, const MixedArgs &A, int batch, int tx0, int ty0, int ty,
                                             int ix, int iya, int iyb, float2 C[NF][kOrders])
@@ -1579,7 +1577,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
 // Facet generator of the mixed path: same Taylor expansion, states written out
 // ([np][NF][n_facets]).
 template <int V>
-__global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
+__global__ void __launch_bounds__(NT, Var<V>::CWM ? 1 : 3)
     generate_mixed_kernel(MixedArgs A, int n0, int np, int b0, float *state)
 {
     constexpr int NF = Var<V>::NF;
@@ -1598,23 +1596,29 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     const int iya = ty0 + 2 * warp, iyb = iya + 1;
     const bool va = ix < S.nx && iya < S.ny, vb = ix < S.nx && iyb < S.ny;
     float2 C[NF][kOrders];
-    item_coeffs<NF, 8>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, C);
+    item_coeffs<NF, 4>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, C);
+    // the window's pulse times, staged in the (now free) chunk region
+    float *tau_s = reinterpret_cast<float *>(sm.w);
+    __syncthreads();
+    for (int i = threadIdx.x; i < pe - pa; i += NT) tau_s[i] = A.tau[pa + i];
+    __syncthreads();
     const int64_t nf = (int64_t)S.nx * S.ny;
+    const int64_t fa = (int64_t)iya * S.nx + ix, fb = (int64_t)iyb * S.nx + ix;
+    // states are written once and not read back here: streaming stores
+#pragma unroll 4
     for (int n = pa; n < pe; ++n) {
-        const float2 t = dup(A.tau[n]);
+        const float2 t = dup(tau_s[n - pa]);
         float *o = state + (size_t)(n - n0) * NF * nf;
         float2 st[NF];
 #pragma unroll
         for (int q = 0; q < NF; ++q) st[q] = horner2(C[q], t);
         if (va) {
-            const int64_t f = (int64_t)iya * S.nx + ix;
 #pragma unroll
-            for (int q = 0; q < NF; ++q) o[q * nf + f] = st[q].x;
+            for (int q = 0; q < NF; ++q) __stcs(o + q * nf + fa, st[q].x);
         }
         if (vb) {
-            const int64_t f = (int64_t)iyb * S.nx + ix;
 #pragma unroll
-            for (int q = 0; q < NF; ++q) o[q * nf + f] = st[q].y;
+            for (int q = 0; q < NF; ++q) __stcs(o + q * nf + fb, st[q].y);
         }
     }
 }
@@ -1625,7 +1629,8 @@ MixedArgs make_args(const DevScene &S, const MixedTables &M)
     A.S = S;
     A.ex = M.ex;
     A.ey = M.ey;
-    A.wt = M.wt;
+    A.tc = M.tc;
+    A.cr = M.cr;
     A.tau = M.tau;
     A.nb = M.nb;
     A.n_batches = M.n_batches;

@@ -216,45 +216,55 @@ harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps,
     M.n_batches = (np + M.nb - 1) / M.nb;
     M.nf = nf;
     const size_t nsw = (size_t)nsets * std::max(nw, 1);
-    // Taylor tables: E_{w,o} = e^{-i omega t_c} (-i omega)^o / o! about the batch
-    // centre t_c, times the complex factor c_f of each field (state field f =
-    // Re(c_f Q E) for the component phasor Q): eta (1), eta_x (i kx), eta_y (i ky),
-    // and with the Choppy Wave Model D_x (i kx/k), D_y (i ky/k), dD_x/dx (-kx^2/k),
-    // dD_x/dy (-kx ky/k), dD_y/dy (-ky^2/k).
+    // Taylor tables. With the component's space phasor q (e^{i kx x} a e^{i (ky y +
+    // phi)}) and Q = q e^{-i omega t_c} at the batch centre t_c, state field f at
+    // time offset tau is Re(c_f Q e^{-i omega tau}) summed over components, and
+    // e^{-i omega tau} = sum_o (-i)^o r_o tau^o with r_o = omega^o / o!. The field
+    // factor c_f is real (eta: 1; with the Choppy Wave Model dD_x/dx: -kx^2/k,
+    // dD_x/dy: -kx ky/k, dD_y/dy: -ky^2/k) or imaginary, c_f = i g (eta_x: kx,
+    // eta_y: ky; D_x: kx/k, D_y: ky/k). So each Taylor coefficient is a real number
+    // times Q_r or Q_i: Re(Q (-i)^o) = Q_r, Q_i, -Q_r, -Q_i, Q_r, Q_i and
+    // Re(i Q (-i)^o) = -Q_i, Q_r, Q_i, -Q_r, -Q_i, Q_r for o = 0..5. Tables:
+    // tc[b][set][m] = e^{-i omega t_c(b)}; cr[set][m][f][o] = the signed real factor
+    // (c or g) r_o (the kernels pair orders 2p, 2p + 1 with (Q_r, Q_i) for real c_f
+    // and with (Q_i, Q_r) for imaginary c_f).
     std::vector<float> tau(np);
-    std::vector<float2> wt((size_t)M.n_batches * nsw * nf * kOrders);
+    std::vector<float2> tc((size_t)M.n_batches * nsw);
+    std::vector<float> cr(nsw * nf * kOrders);
     for (int b = 0; b < M.n_batches; ++b) {
         int first = b * M.nb, last = std::min(np, first + M.nb) - 1;
-        double tc = 0.5 * (ps[first].ts + ps[last].ts);
-        for (int n = first; n <= last; ++n) tau[n] = (float)(ps[n].ts - tc);
+        double tcb = 0.5 * (ps[first].ts + ps[last].ts);
+        for (int n = first; n <= last; ++n) tau[n] = (float)(ps[n].ts - tcb);
         for (int q = 0; q < nsets; ++q)
             for (int m = 0; m < nw; ++m) {
-                const Wave &w = W.at(q, m);
-                const double k = std::sqrt(w.kx * w.kx + w.ky * w.ky);
-                // c_f = (cr, ci)
-                const double cf[8][2] = {{1.0, 0.0},          {0.0, w.kx},          {0.0, w.ky},
-                                         {0.0, w.kx / k},     {0.0, w.ky / k},      {-w.kx * w.kx / k, 0.0},
-                                         {-w.kx * w.ky / k, 0.0}, {-w.ky * w.ky / k, 0.0}};
-                double er = std::cos(-w.om * tc), ei = std::sin(-w.om * tc);
-                for (int o = 0; o < kOrders; ++o) {
-                    if (o > 0) {
-                        // multiply by (-i omega) / o
-                        double nr = w.om * ei / o, ni = -w.om * er / o;
-                        er = nr;
-                        ei = ni;
-                    }
-                    const size_t base = ((((size_t)b * nsets + q) * nw + m) * nf) * kOrders + o;
-                    for (int f = 0; f < nf; ++f) {
-                        const double vr = cf[f][0] * er - cf[f][1] * ei, vi = cf[f][0] * ei + cf[f][1] * er;
-                        wt[base + (size_t)f * kOrders] = make_float2((float)vr, (float)vi);
-                    }
-                }
+                const double a = -W.at(q, m).om * tcb;
+                tc[(size_t)b * nsw + (size_t)q * nw + m] = make_float2((float)std::cos(a), (float)std::sin(a));
             }
     }
+    static const double kSignReal[kOrders] = {1.0, 1.0, -1.0, -1.0, 1.0, 1.0};
+    static const double kSignImag[kOrders] = {-1.0, 1.0, 1.0, -1.0, -1.0, 1.0};
+    for (int q = 0; q < nsets; ++q)
+        for (int m = 0; m < nw; ++m) {
+            const Wave &w = W.at(q, m);
+            const double k = std::sqrt(w.kx * w.kx + w.ky * w.ky);
+            // factor c (real c_f) or g (c_f = i g) of each field
+            const double g[8] = {1.0, w.kx, w.ky, w.kx / k, w.ky / k, -w.kx * w.kx / k, -w.kx * w.ky / k,
+                                 -w.ky * w.ky / k};
+            double r = 1.0;  // omega^o / o!
+            for (int o = 0; o < kOrders; ++o) {
+                if (o > 0) r *= w.om / o;
+                for (int f = 0; f < nf; ++f) {
+                    const bool real = f == 0 || f >= 5;
+                    const double sg = real ? kSignReal[o] : kSignImag[o];
+                    cr[(((size_t)q * nw + m) * nf + f) * kOrders + o] = (float)(sg * g[f] * r);
+                }
+            }
+        }
     fit_taps(s->dev, M.tap);
     fit_sinc2(M.sinc2);
     if (phasor_tables<float2>(s, W, nullptr, &M.ex, &M.ey, nullptr) != cudaSuccess ||
-        upload_raw(s, wt, &M.wt) != cudaSuccess || upload_raw(s, tau, &M.tau) != cudaSuccess)
+        upload_raw(s, tc, &M.tc) != cudaSuccess || upload_raw(s, cr, &M.cr) != cudaSuccess ||
+        upload_raw(s, tau, &M.tau) != cudaSuccess)
         return HARM_E_CUDA;
     return HARM_OK;
 }

@@ -22,7 +22,8 @@ struct MixedTables {
     int tile_x = 32, tile_y = 16;
     const float2 *ex = nullptr;   // [n_sets][nw][nx]  e^{i kx x}
     const float2 *ey = nullptr;   // [n_sets][nw][ny]  a e^{i phi} e^{i ky y}
-    const float2 *wt = nullptr;   // [n_batches][n_sets][nw][nf][kOrders] Taylor coefficients
+    const float2 *tc = nullptr;   // [n_batches][n_sets][nw] e^{-i omega t_c} at the batch centre
+    const float *cr = nullptr;    // [n_sets][nw][nf][kOrders] signed real Taylor coefficients
     const float *tau = nullptr;   // [np_total] t_s(n) - t_centre(batch)
     float tap[8][kTapDeg + 1];    // Kaiser-sinc tap h(j - f), j = -3..4, monomials in t
     float sinc2[kSincDeg + 1];    // sinc^2(x) for |x| <= 1, monomials in t = 2 x^2 - 1
