@@ -193,6 +193,25 @@ def run_oracle_sample(desc, n_pulses_sample):
     return {"pulses": pulses, "iq": iq, "seconds": dt, "units": units, "cores": oracle.num_threads()}
 
 
+def run_oracle_single_core():
+    """The oracle on one host core: the headline scene's geometry, waves and 6
+    channels on a 400 x 200 facet patch (same work per contribution), 2 pulses."""
+    import oracle
+    d = hs.ati_scene(nx=400, ny=200)
+    pulses = [0, d["n_pulses"] // 2]
+    prev = oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.echo(d, pulses)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(prev)
+    units = hs.n_facets(d) * len(pulses) * len(d["rx"])
+    return {"value": units / dt, "unit": UNIT, "cores": 1,
+            "sample": "2 pulses x 400 x 200 facets x %d channels of the headline scene's setup (%.1f s)" % (
+                len(d["rx"]), dt)}
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return
@@ -381,7 +400,8 @@ def main():
         line["cpu_baseline"] = {"value": cpu["units"] / cpu["seconds"], "unit": UNIT, "cores": cpu["cores"],
                                 "kind": "oracle",
                                 "sample": "%d pulse(s) of the workload x %d facets x %d channels (%.1f s)" % (
-                                    len(cpu["pulses"]), hs.n_facets(desc), nc, cpu["seconds"])}
+                                    len(cpu["pulses"]), hs.n_facets(desc), nc, cpu["seconds"]),
+                                "single_core": run_oracle_single_core()}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

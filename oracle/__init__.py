@@ -132,6 +132,8 @@ def lib():
         L.or_echo.restype = C.c_int
         L.or_contribution.argtypes = [C.POINTER(OrScene), C.c_int, C.c_int, C.c_int64, dp, dp]
         L.or_num_threads.restype = C.c_int
+        L.or_set_num_threads.argtypes = [C.c_int]
+        L.or_set_num_threads.restype = None
         L.or_adjoint.argtypes = [C.POINTER(OrScene), C.c_int, C.POINTER(C.c_int), dp, dp, dp]
         L.or_adjoint.restype = C.c_int
         _lib = L
@@ -381,6 +383,13 @@ def echo(desc, pulses, facets=None):
 
 def num_threads():
     return lib().or_num_threads()
+
+
+def set_num_threads(n):
+    """Threads of later oracle calls (timing only); returns the previous count."""
+    prev = num_threads()
+    lib().or_set_num_threads(int(n))
+    return prev
 
 
 def adjoint(desc, pulses, resid):

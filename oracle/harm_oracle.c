@@ -818,6 +818,16 @@ int or_num_threads(void)
 #endif
 }
 
+/* Threads of later parallel regions (timing only; results do not depend on it). */
+void or_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Adjoint of the echo with respect to the per-cell NRCS base and current, for
    the misfit L = sum |IQ - target|^2 with residual r = IQ - target given as
    resid[c][i][k][2] for the listed pulses. Chain rule on each contribution s
