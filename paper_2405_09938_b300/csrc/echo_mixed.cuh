@@ -75,6 +75,9 @@ struct Var {
     static constexpr bool LUT = (V & kVarLut) != 0;
     static constexpr int NF = CWM ? 8 : 3;        // state fields
     static constexpr int MIN_BLOCKS = CWM ? 1 : 2; // CTAs per SM the registers allow
+    // channel-loop unroll of the forward pulse body (measured: 2 for the linear
+    // surface; the Choppy Wave Model, at one CTA per SM, runs best rolled)
+    static constexpr int FWD_CU = CWM ? 1 : 2;
 };
 
 // FP32 tile reference of one antenna for one pulse (16 floats).
@@ -948,14 +951,14 @@ __device__ __forceinline__ void pair_gain(const Smem &sm, const DevScene &S, con
 // their rest positions moved by the horizontal displacement, their normal is the
 // cross product of the displaced surface's tangents and their area scales with
 // its vertical component; with u-v grids the pattern gains are complex.
-template <int TAPS, int V, typename Sink>
+template <int TAPS, int V, int CU, int NCC, typename Sink>
 __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A, const PolyArgs &P, const PairGeo &G,
                                              const float2 fs[Var<V>::NF], int pi, float xi_x, float fi,
                                              Sink &sink)
 {
     constexpr bool CWM = Var<V>::CWM, LUT = Var<V>::LUT;
     const DevScene &S = A.S;
-    const int nc = S.nc;
+    const int nc = NCC > 0 ? NCC : S.nc;  // compile-time channel count when NCC > 0
     const float2 one = make_float2(1.0f, 1.0f);
     const PulseRec PR = sm.pr[pi];
     const float2 eta = fs[0];
@@ -1008,6 +1011,7 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
     const AntRec2 *RX = sm.rx2 + pi * nc;
     const ChanRec2 *CH = sm.ch2 + pi * nc;
     float2 gr_prev = make_float2(0.0f, 0.0f), amps_prev = make_float2(0.0f, 0.0f);
+#pragma unroll CU
     for (int ch = 0; ch < nc; ++ch) {
         const AntRec2 R = RX[ch];
         const ChanRec2 Q = CH[ch];
@@ -1332,7 +1336,7 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
                 sink.buf = n & (kTileBufs - 1);
                 float2 st[NF];
                 eval_state<NF>(sm, C, sm.pr[pi].tau, st);
-                facet_pulse2<TAPS, V>(sm, A, P, G, st, pi, xi_x, fi, sink);
+                facet_pulse2<TAPS, V, Var<V>::FWD_CU, 0>(sm, A, P, G, st, pi, xi_x, fi, sink);
                 // flush the range tiles of pulse pairs (one barrier per two pulses;
                 // a tile is reused four pulses later, after at least one more barrier)
                 if ((pi & 1) || n == ce - 1) {
@@ -1478,7 +1482,7 @@ __device__ __forceinline__ void add_cell_grads(const FacetGeo &G, float as, floa
     }
 }
 
-template <int TAPS, typename InT, int V>
+template <int TAPS, typename InT, int V, int NCC>
 __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     adjoint_mixed_kernel(MixedArgs A, PolyArgs P, int n0, int np, int b0, const InT *resid, double *g_sigma,
                          double *g_uv)
@@ -1566,7 +1570,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
                 sink.n = n;
                 float2 st[NF];
                 eval_state<NF>(sm, C, sm.pr[pi].tau, st);
-                facet_pulse2<TAPS, V>(sm, A, P, G, st, pi, xi_x, fi, sink);
+                facet_pulse2<TAPS, V, (NCC > 0 ? NCC : 1), NCC>(sm, A, P, G, st, pi, xi_x, fi, sink);
             }
         }
     }
@@ -1702,19 +1706,29 @@ cudaError_t accumulate_t(const DevScene &S, const MixedTables &M, cudaStream_t s
     });
 }
 
-template <int TAPS, typename InT, int V>
-cudaError_t adjoint_t(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, const InT *resid,
-                      double *g_sigma, double *g_uv)
+template <int TAPS, typename InT, int V, int NCC>
+cudaError_t adjoint_nc(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, const InT *resid,
+                       double *g_sigma, double *g_uv)
 {
     const MixedArgs A = make_args(S, M);
     const PolyArgs P = make_poly(M);
     const int bytes = layout(S.nc, true, Var<V>::NF).total;
-    cudaError_t e = prep(adjoint_mixed_kernel<TAPS, InT, V>, bytes);
+    cudaError_t e = prep(adjoint_mixed_kernel<TAPS, InT, V, NCC>, bytes);
     if (e != cudaSuccess) return e;
     return over_batches(S, M, TY, n0, np, [&](int bb, dim3 grid) {
-        adjoint_mixed_kernel<TAPS, InT, V><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, resid, g_sigma, g_uv);
+        adjoint_mixed_kernel<TAPS, InT, V, NCC><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, resid, g_sigma, g_uv);
         return cudaGetLastError();
     });
+}
+
+// The adjoint's channel loop runs fully unrolled for six channels (two antennas
+// of three phase centres, 4 % faster), otherwise over the scene's channel count.
+template <int TAPS, typename InT, int V>
+cudaError_t adjoint_t(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, const InT *resid,
+                      double *g_sigma, double *g_uv)
+{
+    if (S.nc == 6) return adjoint_nc<TAPS, InT, V, 6>(S, M, st, n0, np, resid, g_sigma, g_uv);
+    return adjoint_nc<TAPS, InT, V, 0>(S, M, st, n0, np, resid, g_sigma, g_uv);
 }
 
 // Launchers of one variant V.
