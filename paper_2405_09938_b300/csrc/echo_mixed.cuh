@@ -1262,7 +1262,7 @@ __device__ __forceinline__ void eval_state(const Smem &sm, const float2 C[NF][kO
 
 // One forward work item (tile x pulse batch) of one scene. Every thread of the
 // CTA calls it; it starts and ends with the CTA's range tiles all zero.
-template <int TAPS, typename OutT, int V>
+template <int TAPS, typename OutT, int V, int NCC = 0>
 __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs &P, const ItemGeo &I, int n0, int np,
                              OutT *iq)
 {
@@ -1336,7 +1336,7 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
                 sink.buf = n & (kTileBufs - 1);
                 float2 st[NF];
                 eval_state<NF>(sm, C, sm.pr[pi].tau, st);
-                facet_pulse2<TAPS, V, Var<V>::FWD_CU, 0>(sm, A, P, G, st, pi, xi_x, fi, sink);
+                facet_pulse2<TAPS, V, Var<V>::FWD_CU, NCC>(sm, A, P, G, st, pi, xi_x, fi, sink);
                 // flush the range tiles of pulse pairs (one barrier per two pulses;
                 // a tile is reused four pulses later, after at least one more barrier)
                 if ((pi & 1) || n == ce - 1) {
@@ -1368,7 +1368,7 @@ __device__ __forceinline__ void clear_smem(const Smem &sm, int nc)
     for (int i = threadIdx.x; i < NWARP * SBINS * SROW; i += NT) sm.stage[i] = 0.0f;
 }
 
-template <int TAPS, typename OutT, int V>
+template <int TAPS, typename OutT, int V, int NCC>
 __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     accumulate_mixed_kernel(MixedArgs A, PolyArgs P, int n0, int np, int b0, int ty, OutT *iq)
 {
@@ -1377,7 +1377,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     const ItemGeo I = item_geo(A, blockIdx.x, b0 + blockIdx.y, ty, n0, np);
     if (I.pa >= I.pe) return;
     clear_smem(sm, A.S.nc);
-    forward_item<TAPS, OutT, V>(sm, A, P, I, n0, np, iq);
+    forward_item<TAPS, OutT, V, NCC>(sm, A, P, I, n0, np, iq);
 }
 
 // Work list of a batched launch: scene s owns items [start[s], start[s + 1]);
@@ -1692,18 +1692,29 @@ cudaError_t over_batches(const DevScene &S, const MixedTables &M, int ty, int n0
     return cudaSuccess;
 }
 
-template <int TAPS, typename OutT, int V>
-cudaError_t accumulate_t(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, OutT *iq)
+template <int TAPS, typename OutT, int V, int NCC>
+cudaError_t accumulate_nc(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, OutT *iq)
 {
     const MixedArgs A = make_args(S, M);
     const PolyArgs P = make_poly(M);
     const int bytes = layout(S.nc, true, Var<V>::NF).total;
-    cudaError_t e = prep(accumulate_mixed_kernel<TAPS, OutT, V>, bytes);
+    cudaError_t e = prep(accumulate_mixed_kernel<TAPS, OutT, V, NCC>, bytes);
     if (e != cudaSuccess) return e;
     return over_batches(S, M, TY, n0, np, [&](int bb, dim3 grid) {
-        accumulate_mixed_kernel<TAPS, OutT, V><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, TY, iq);
+        accumulate_mixed_kernel<TAPS, OutT, V, NCC><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, TY, iq);
         return cudaGetLastError();
     });
+}
+
+// Six channels (two receive antennas of three phase centres) get their own
+// instantiation with a compile-time channel count (0.7 % faster than the loop
+// over the scene's count); other counts and the box taps use the general one.
+template <int TAPS, typename OutT, int V>
+cudaError_t accumulate_t(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, OutT *iq)
+{
+    if constexpr (TAPS == 8)
+        if (S.nc == 6) return accumulate_nc<TAPS, OutT, V, 6>(S, M, st, n0, np, iq);
+    return accumulate_nc<TAPS, OutT, V, 0>(S, M, st, n0, np, iq);
 }
 
 template <int TAPS, typename InT, int V, int NCC>
@@ -1727,7 +1738,8 @@ template <int TAPS, typename InT, int V>
 cudaError_t adjoint_t(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, const InT *resid,
                       double *g_sigma, double *g_uv)
 {
-    if (S.nc == 6) return adjoint_nc<TAPS, InT, V, 6>(S, M, st, n0, np, resid, g_sigma, g_uv);
+    if constexpr (TAPS == 8)
+        if (S.nc == 6) return adjoint_nc<TAPS, InT, V, 6>(S, M, st, n0, np, resid, g_sigma, g_uv);
     return adjoint_nc<TAPS, InT, V, 0>(S, M, st, n0, np, resid, g_sigma, g_uv);
 }
 
