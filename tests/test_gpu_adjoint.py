@@ -75,6 +75,20 @@ def test_adjoint_matches_oracle_adjoint(taps):
     assert np.linalg.norm(guv_g - guv_o) <= 1e-3 * np.linalg.norm(guv_o)
 
 
+def test_adjoint_three_channels():
+    # one receive antenna (3 phase centres): the general channel loop of the
+    # adjoint (six-channel scenes run a fully unrolled instantiation)
+    d = _scene(n_pulses=40, nx=64, ny=48)
+    tx, rx = hs.geometry(d["n_pulses"], ("A",), (-hs.PHASE_CENTRE_SPACING_M, 0.0, hs.PHASE_CENTRE_SPACING_M))
+    d["tx"], d["rx"] = tx, rx
+    pulses = list(range(40))
+    r = oracle.echo(d, pulses) - oracle.echo(_perturbed(d), pulses)
+    gs_o, guv_o = oracle.adjoint(d, pulses, r)
+    gs_g, guv_g = _gpu_adjoint(d, 0, 40, r)
+    assert np.abs(gs_g - gs_o).max() <= TOL_GRAD * np.abs(gs_o).max()
+    assert np.abs(guv_g - guv_o).max() <= TOL_GRAD * np.abs(guv_o).max()
+
+
 def test_adjoint_unaligned_window():
     d = _scene(n_pulses=100, nx=45, ny=30)
     pulses = list(range(17, 70))
