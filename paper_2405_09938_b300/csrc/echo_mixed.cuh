@@ -1397,7 +1397,7 @@ struct BatchItems {
 // Persistent batched forward launch: a fixed pool of CTAs pulls work items from
 // a global counter until the list is exhausted (no waiting on other CTAs). The
 // scene arguments of the current item are copied to shared memory.
-template <int TAPS, int V>
+template <int TAPS, int V, int NCC>
 __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     batch_mixed_kernel(BatchItems B, PolyArgs P, unsigned int *counter)
 {
@@ -1441,7 +1441,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
         const int local = it - B.start[k];
         const int tiles = B.tiles[scene];
         const ItemGeo I = item_geo(args, local % tiles, local / tiles, B.ty[scene], 0, args.S.np_total);
-        if (I.pa < I.pe) forward_item<TAPS, float, V>(sm, args, P, I, 0, args.S.np_total, B.iq[scene]);
+        if (I.pa < I.pe) forward_item<TAPS, float, V, NCC>(sm, args, P, I, 0, args.S.np_total, B.iq[scene]);
         __syncthreads();
     }
 }
@@ -1796,11 +1796,14 @@ struct MixedLaunch {
         const int bytes = layout(L.nc, true, Var<V>::NF).total;
         cudaError_t e;
         if (L.taps == 1) {
-            if ((e = prep(batch_mixed_kernel<1, V>, bytes)) != cudaSuccess) return e;
-            batch_mixed_kernel<1, V><<<L.ctas, NT, bytes, st>>>(B, P, L.counter);
+            if ((e = prep(batch_mixed_kernel<1, V, 0>, bytes)) != cudaSuccess) return e;
+            batch_mixed_kernel<1, V, 0><<<L.ctas, NT, bytes, st>>>(B, P, L.counter);
+        } else if (L.nc == 6) {  // compile-time channel count, as for single scenes
+            if ((e = prep(batch_mixed_kernel<8, V, 6>, bytes)) != cudaSuccess) return e;
+            batch_mixed_kernel<8, V, 6><<<L.ctas, NT, bytes, st>>>(B, P, L.counter);
         } else {
-            if ((e = prep(batch_mixed_kernel<8, V>, bytes)) != cudaSuccess) return e;
-            batch_mixed_kernel<8, V><<<L.ctas, NT, bytes, st>>>(B, P, L.counter);
+            if ((e = prep(batch_mixed_kernel<8, V, 0>, bytes)) != cudaSuccess) return e;
+            batch_mixed_kernel<8, V, 0><<<L.ctas, NT, bytes, st>>>(B, P, L.counter);
         }
         return cudaGetLastError();
     }
