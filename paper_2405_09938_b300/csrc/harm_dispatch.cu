@@ -277,8 +277,13 @@ cudaError_t launch_generate(harm_scene *s, int n0, int np, void *state)
 
 cudaError_t launch_accumulate(harm_scene *s, int n0, int np, void *iq, harm_dtype dtype)
 {
-    if (s->desc.precision == HARM_PREC_FP64) return launch_accumulate_f64(s->dev, s->stream, n0, np, iq, dtype);
-    return launch_accumulate_mixed(s->dev, s->mixed, s->stream, n0, np, iq, dtype);
+    return launch_accumulate_on(s, s->stream, n0, np, iq, dtype);
+}
+
+cudaError_t launch_accumulate_on(harm_scene *s, cudaStream_t st, int n0, int np, void *iq, harm_dtype dtype)
+{
+    if (s->desc.precision == HARM_PREC_FP64) return launch_accumulate_f64(s->dev, st, n0, np, iq, dtype);
+    return launch_accumulate_mixed(s->dev, s->mixed, st, n0, np, iq, dtype);
 }
 
 cudaError_t launch_adjoint(harm_scene *s, int n0, int np, const void *resid, harm_dtype dtype, double *g_sigma,

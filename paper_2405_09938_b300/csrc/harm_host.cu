@@ -1,15 +1,19 @@
 // Echo into host memory: the burst is computed in pulse blocks into a ring of two
 // device buffers owned by the scene, and each block is copied to the caller's
-// page-locked host array on a second stream while the next block is computed
+// page-locked host array on a copy stream while the next block is computed
 // (the raw-data output stage of Sec. IV-B: the GPU keeps computing while earlier
-// parts of the echo leave it).
+// parts of the echo leave it). Even blocks run on the scene's stream, odd blocks
+// on a second compute stream, so that one block's last wave of CTAs overlaps the
+// next block's first.
 //
-// Ordering (all on the device, no host waits inside the call):
-//   scene stream : [wait free[b]] memset(ring[b]) accumulate(block k) record ready[b]
-//   copy stream  : wait ready[b]  copy ring[b] -> host block k    record free[b]
-// with b = k mod 2; at the end the scene stream waits for both free events, so
-// whatever the caller orders after the call on the scene stream (and
-// harm_scene_sync) sees the host array complete.
+// Ordering (all on the device, no host waits inside the call), b = k mod 2,
+// compute stream c[b] (c[0] = the scene's stream, c[1] = the second one, which
+// first waits for everything ordered before the call on the scene's stream):
+//   c[b]        : [wait free[b]] memset(ring[b]) accumulate(block k) record ready[b]
+//   copy stream : wait ready[b]  copy ring[b] -> host block k    record free[b]
+// At the end the scene stream waits for both free events (each copy follows its
+// block's computation), so whatever the caller orders after the call on the scene
+// stream (and harm_scene_sync) sees the host array complete.
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
@@ -64,12 +68,15 @@ int block_size(int np, int block_pulses)
 harm_status ensure_ring(harm_scene *s, size_t bytes)
 {
     if (!s->copy_stream) HCUDA(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking), "copy stream");
+    if (!s->aux_stream) HCUDA(cudaStreamCreateWithFlags(&s->aux_stream, cudaStreamNonBlocking), "compute stream");
+    if (!s->fork) HCUDA(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming), "event");
     for (int b = 0; b < 2; ++b) {
         if (!s->ring_ready[b]) HCUDA(cudaEventCreateWithFlags(&s->ring_ready[b], cudaEventDisableTiming), "event");
         if (!s->ring_free[b]) HCUDA(cudaEventCreateWithFlags(&s->ring_free[b], cudaEventDisableTiming), "event");
     }
     if (s->ring_bytes >= bytes) return HARM_OK;
     HCUDA(cudaStreamSynchronize(s->copy_stream), "wait for earlier host copies");
+    HCUDA(cudaStreamSynchronize(s->aux_stream), "wait for the second compute stream");
     HCUDA(cudaStreamSynchronize(s->stream), "wait for the scene stream");
     for (int b = 0; b < 2; ++b) {
         if (s->ring[b]) cudaFree(s->ring[b]);
@@ -87,6 +94,7 @@ namespace harm {
 
 void release_host_ring(harm_scene *s)
 {
+    if (s->aux_stream) cudaStreamSynchronize(s->aux_stream);
     if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
     for (int b = 0; b < 2; ++b) {
         if (s->ring[b]) cudaFree(s->ring[b]);
@@ -96,7 +104,10 @@ void release_host_ring(harm_scene *s)
         s->ring_ready[b] = s->ring_free[b] = nullptr;
     }
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
-    s->copy_stream = nullptr;
+    if (s->aux_stream) cudaStreamDestroy(s->aux_stream);
+    if (s->fork) cudaEventDestroy(s->fork);
+    s->copy_stream = s->aux_stream = nullptr;
+    s->fork = nullptr;
     s->ring_bytes = 0;
 }
 
@@ -127,14 +138,19 @@ extern "C" harm_status harm_echo_accumulate_host(harm_scene *s, int32_t n0, int3
     if (st != HARM_OK) return st;
 
     const int nblocks = (np + B - 1) / B;
+    const cudaStream_t cs[2] = {s->stream, s->aux_stream};
+    if (nblocks > 1) {
+        HCUDA(cudaEventRecord(s->fork, s->stream), "record fork");
+        HCUDA(cudaStreamWaitEvent(s->aux_stream, s->fork, 0), "second compute stream wait");
+    }
     for (int k = 0; k < nblocks; ++k) {
         const int b = k & 1;
         const int p0 = k * B, pb = std::min(B, np - p0);
-        if (k >= 2) HCUDA(cudaStreamWaitEvent(s->stream, s->ring_free[b], 0), "wait for the ring buffer");
-        HCUDA(cudaMemsetAsync(s->ring[b], 0, (size_t)nc * pb * row, s->stream), "clear ring buffer");
-        cudaError_t e = harm::launch_accumulate(s, n0 + p0, pb, s->ring[b], dtype);
+        if (k >= 2) HCUDA(cudaStreamWaitEvent(cs[b], s->ring_free[b], 0), "wait for the ring buffer");
+        HCUDA(cudaMemsetAsync(s->ring[b], 0, (size_t)nc * pb * row, cs[b]), "clear ring buffer");
+        cudaError_t e = harm::launch_accumulate_on(s, cs[b], n0 + p0, pb, s->ring[b], dtype);
         if (e != cudaSuccess) return cuda_fail(e, "echo accumulator launch");
-        HCUDA(cudaEventRecord(s->ring_ready[b], s->stream), "record block ready");
+        HCUDA(cudaEventRecord(s->ring_ready[b], cs[b]), "record block ready");
         HCUDA(cudaStreamWaitEvent(s->copy_stream, s->ring_ready[b], 0), "copy stream wait");
         // block k of every channel: nc rows of pb pulses, strided np pulses apart in iq_host
         HCUDA(cudaMemcpy2DAsync((char *)iq_host + (size_t)p0 * row, (size_t)np * row, s->ring[b], (size_t)pb * row,

@@ -46,8 +46,10 @@ struct harm_scene {
     std::vector<double> r0;
     int64_t nf = 0;
     int nw = 0;
-    // echo into host memory: copy stream and a ring of two device blocks
-    cudaStream_t copy_stream = nullptr;
+    // echo into host memory: a second compute stream (consecutive blocks overlap),
+    // a copy stream and a ring of two device blocks
+    cudaStream_t aux_stream = nullptr, copy_stream = nullptr;
+    cudaEvent_t fork = nullptr;
     void *ring[2] = {nullptr, nullptr};
     size_t ring_bytes = 0;
     cudaEvent_t ring_ready[2] = {nullptr, nullptr}, ring_free[2] = {nullptr, nullptr};
@@ -79,6 +81,7 @@ cudaError_t phasor_tables(harm_scene *s, const WaveSets &W, const PulseState *ps
 
 cudaError_t launch_generate(harm_scene *s, int n0, int np, void *state);
 cudaError_t launch_accumulate(harm_scene *s, int n0, int np, void *iq, harm_dtype dtype);
+cudaError_t launch_accumulate_on(harm_scene *s, cudaStream_t st, int n0, int np, void *iq, harm_dtype dtype);
 cudaError_t launch_adjoint(harm_scene *s, int n0, int np, const void *resid, harm_dtype dtype, double *g_sigma0,
                            double *g_uv);
 
