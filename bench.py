@@ -392,7 +392,7 @@ def main():
         # IQ error of the GPU path on the sampled pulses
         sel = [p - n0_step for p in cpu["pulses"] if n0_step <= p < n0_step + np_step]
         if sel:
-            got = iq.cpu().numpy()[:, sel, :]
+            got = host_iq.numpy()[:, sel, :]  # the end-to-end leg's IQ: one zeroed run
             want = cpu["iq"][:, [i for i, p in enumerate(cpu["pulses"]) if n0_step <= p < n0_step + np_step], :]
             err = float(np.sqrt(np.sum(np.abs(got - want) ** 2) / np.sum(np.abs(want) ** 2)))
             line["iq_rel_rms"] = err
