@@ -193,12 +193,14 @@ harm_status harm_echo_accumulate(harm_scene *scene, int32_t n0, int32_t np, void
    [n_channels][np][n_range] complex of `dtype` (overwritten, not added to). The
    burst runs in blocks of block_pulses pulses (<= 0: about an eighth of the
    burst, a multiple of 128 pulses) into a ring of two device buffers that the
-   scene owns; each block is copied to iq_host on a second stream while the next
-   one is computed. iq_host must be page-locked (cudaHostAlloc / cudaHostRegister)
+   scene owns, alternating between the scene's stream and a second compute
+   stream; each block is copied to iq_host on a copy stream while the next one is
+   computed. iq_host must be page-locked (cudaHostAlloc / cudaHostRegister)
    and stay valid until the scene's stream has passed the call: like every call
    here it is asynchronous, and iq_host is complete after harm_scene_sync (or a
-   wait on the scene's stream). The ring (2 x n_channels x block x n_range
-   elements) is kept for later calls and freed with the scene.
+   wait on the scene's stream, which the call joins to the other two). The ring
+   (2 x n_channels x block x n_range elements) and the streams are kept for later
+   calls and freed with the scene.
    Errors: HARM_E_INVALID (window, NULL or pageable iq_host, dtype), HARM_E_OOM
    (ring allocation), HARM_E_CUDA. */
 harm_status harm_echo_accumulate_host(harm_scene *scene, int32_t n0, int32_t np, void *iq_host,
