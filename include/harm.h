@@ -14,7 +14,8 @@
  *     radars, z up, origin at the scene centre on the mean surface [m].
  *   - Device memory passed in (iq, state, residual, gradients) belongs to the
  *     caller and must be device memory of the current CUDA device. The scene owns
- *     only its own tables; nothing is allocated per call.
+ *     only its own tables (and, once harm_echo_accumulate_host has been called,
+ *     that call's device ring and streams); no other call allocates.
  *   - Every call is asynchronous on the scene's CUDA stream. A returned status
  *     reports launch-time errors; device-side errors are reported by the next
  *     call or by harm_scene_sync().
@@ -136,8 +137,9 @@ typedef struct {
 
 /* Create a scene: validate the descriptor, build the wave component table
    (linear surface, Sec. III), per-pulse platform state with light time (Eq. 3)
-   and range windows in FP64 on the host, and upload them to the current device on
-   `cuda_stream` (a cudaStream_t, NULL = default stream). *out receives the scene.
+   and range windows in FP64 on the host, upload them to the current device on
+   `cuda_stream` (a cudaStream_t, NULL = default stream) and evaluate the separable
+   wave phasor tables there. *out receives the scene.
    Errors: HARM_E_INVALID for a bad descriptor or NULL pointer, HARM_E_OOM,
    HARM_E_CUDA. On error *out is set to NULL and nothing is leaked. */
 harm_status harm_scene_create(const harm_scene_desc *desc, void *cuda_stream, harm_scene **out);
