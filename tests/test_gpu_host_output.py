@@ -106,3 +106,18 @@ def test_host_output_fp64_scene():
     sc.close()
     want = oracle.echo(d, list(range(64)))
     assert rel_rms(got, want) < 1e-7
+
+
+def test_host_output_window_checks():
+    import torch
+    d = _scene()
+    sc = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
+    out = torch.empty((len(d["rx"]), 8, d["n_range"]), dtype=torch.complex64, pin_memory=True)
+    with pytest.raises(harm.HarmError) as e:
+        harm.harm_echo_accumulate_host(sc, d["n_pulses"] - 4, 8, out)  # runs past the burst
+    assert e.value.status == harm.HARM_E_INVALID
+    out.fill_(complex(7.0, 7.0))
+    harm.harm_echo_accumulate_host(sc, 0, 0, out)  # empty window: nothing written
+    harm.harm_scene_sync(sc)
+    sc.close()
+    assert (out.numpy() == np.complex64(7 + 7j)).all()
