@@ -88,6 +88,34 @@ harm_status ensure_ring(harm_scene *s, size_t bytes)
     return HARM_OK;
 }
 
+// Blocks of the burst: compute on alternating streams, copy out on the copy stream.
+harm_status enqueue_blocks(harm_scene *s, int32_t n0, int32_t np, void *iq_host, harm_dtype dtype, int B, size_t row)
+{
+    const int nc = s->desc.n_channels;
+    const int nblocks = (np + B - 1) / B;
+    const cudaStream_t cs[2] = {s->stream, s->aux_stream};
+    if (nblocks > 1) {
+        HCUDA(cudaEventRecord(s->fork, s->stream), "record fork");
+        HCUDA(cudaStreamWaitEvent(s->aux_stream, s->fork, 0), "second compute stream wait");
+    }
+    for (int k = 0; k < nblocks; ++k) {
+        const int b = k & 1;
+        const int p0 = k * B, pb = std::min(B, np - p0);
+        if (k >= 2) HCUDA(cudaStreamWaitEvent(cs[b], s->ring_free[b], 0), "wait for the ring buffer");
+        HCUDA(cudaMemsetAsync(s->ring[b], 0, (size_t)nc * pb * row, cs[b]), "clear ring buffer");
+        cudaError_t e = harm::launch_accumulate_on(s, cs[b], n0 + p0, pb, s->ring[b], dtype);
+        if (e != cudaSuccess) return cuda_fail(e, "echo accumulator launch");
+        HCUDA(cudaEventRecord(s->ring_ready[b], cs[b]), "record block ready");
+        HCUDA(cudaStreamWaitEvent(s->copy_stream, s->ring_ready[b], 0), "copy stream wait");
+        // block k of every channel: nc rows of pb pulses, strided np pulses apart in iq_host
+        HCUDA(cudaMemcpy2DAsync((char *)iq_host + (size_t)p0 * row, (size_t)np * row, s->ring[b], (size_t)pb * row,
+                                (size_t)pb * row, nc, cudaMemcpyDeviceToHost, s->copy_stream),
+              "copy block to host");
+        HCUDA(cudaEventRecord(s->ring_free[b], s->copy_stream), "record block copied");
+    }
+    return HARM_OK;
+}
+
 }  // namespace
 
 namespace harm {
@@ -137,28 +165,14 @@ extern "C" harm_status harm_echo_accumulate_host(harm_scene *s, int32_t n0, int3
     harm_status st = ensure_ring(s, (size_t)nc * B * row);
     if (st != HARM_OK) return st;
 
-    const int nblocks = (np + B - 1) / B;
-    const cudaStream_t cs[2] = {s->stream, s->aux_stream};
-    if (nblocks > 1) {
-        HCUDA(cudaEventRecord(s->fork, s->stream), "record fork");
-        HCUDA(cudaStreamWaitEvent(s->aux_stream, s->fork, 0), "second compute stream wait");
-    }
-    for (int k = 0; k < nblocks; ++k) {
-        const int b = k & 1;
-        const int p0 = k * B, pb = std::min(B, np - p0);
-        if (k >= 2) HCUDA(cudaStreamWaitEvent(cs[b], s->ring_free[b], 0), "wait for the ring buffer");
-        HCUDA(cudaMemsetAsync(s->ring[b], 0, (size_t)nc * pb * row, cs[b]), "clear ring buffer");
-        cudaError_t e = harm::launch_accumulate_on(s, cs[b], n0 + p0, pb, s->ring[b], dtype);
-        if (e != cudaSuccess) return cuda_fail(e, "echo accumulator launch");
-        HCUDA(cudaEventRecord(s->ring_ready[b], cs[b]), "record block ready");
-        HCUDA(cudaStreamWaitEvent(s->copy_stream, s->ring_ready[b], 0), "copy stream wait");
-        // block k of every channel: nc rows of pb pulses, strided np pulses apart in iq_host
-        HCUDA(cudaMemcpy2DAsync((char *)iq_host + (size_t)p0 * row, (size_t)np * row, s->ring[b], (size_t)pb * row,
-                                (size_t)pb * row, nc, cudaMemcpyDeviceToHost, s->copy_stream),
-              "copy block to host");
-        HCUDA(cudaEventRecord(s->ring_free[b], s->copy_stream), "record block copied");
-    }
-    for (int b = 0; b < std::min(nblocks, 2); ++b)
-        HCUDA(cudaStreamWaitEvent(s->stream, s->ring_free[b], 0), "join the copy stream");
+    const harm_status qs = enqueue_blocks(s, n0, np, iq_host, dtype, B, row);
+    // join the second compute stream and the copy stream back into the scene's
+    // stream, also after a failed launch, so that harm_scene_sync covers them
+    cudaError_t e = cudaEventRecord(s->fork, s->aux_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->fork, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(s->fork, s->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->fork, 0);
+    if (qs != HARM_OK) return qs;
+    if (e != cudaSuccess) return cuda_fail(e, "join the host-output streams");
     return HARM_OK;
 }
