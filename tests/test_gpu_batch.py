@@ -79,6 +79,11 @@ def test_batch_tune_and_graph_replay():
     harm.harm_batch_run(b, iqs)
     torch.cuda.synchronize()
     first = [t.cpu().numpy() for t in iqs]
+    # the tuned tile heights (8-row tiles run one facet per thread) against the
+    # single-scene accumulator
+    print("tuned tile rows:", rows)
+    for d, a in zip(descs, first):
+        assert rel_rms(a, _single(d)) < 1e-5
     harm.harm_batch_run(b, iqs)  # graph replay
     torch.cuda.synchronize()
     for a, t in zip(first, iqs):
