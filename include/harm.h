@@ -245,6 +245,14 @@ harm_status harm_batch_tune(harm_batch *batch, void *const *iq_dev);
 /* Tile heights chosen for each scene (rows[n_scenes], host memory). */
 harm_status harm_batch_tile_rows(const harm_batch *batch, int32_t *rows);
 
+/* Set the tile height of each scene (rows[n_scenes], host memory, each 8 or 16
+   facet rows) instead of tuning: 16-row tiles run two facets per thread on
+   adjacent rows, 8-row tiles one (less padding on scenes few rows high). The
+   next harm_batch_run captures its graph again. Synchronous with respect to the
+   batch's earlier launches. Errors: HARM_E_INVALID (NULL, a value other than 8 or
+   16), HARM_E_CUDA. */
+harm_status harm_batch_set_tile_rows(harm_batch *batch, const int32_t *rows);
+
 /* Echo of every scene over its full burst into iq_dev[s] (complex64, device),
    as one persistent launch replayed from a CUDA graph; the graph is captured on
    the first call and again whenever the output pointers or zero_first change.

@@ -241,6 +241,19 @@ harm_status harm_batch_tile_rows(const harm_batch *b, int32_t *rows)
     return HARM_OK;
 }
 
+harm_status harm_batch_set_tile_rows(harm_batch *b, const int32_t *rows)
+{
+    if (!b || !rows) return fail(HARM_E_INVALID, "NULL argument");
+    const int n = (int)b->scenes.size();
+    for (int s = 0; s < n; ++s)
+        if (rows[s] != 8 && rows[s] != 16) return fail(HARM_E_INVALID, "tile rows of scene %d: %d (8 or 16)", s, rows[s]);
+    BCUDA(cudaStreamSynchronize(b->stream), "sync");
+    drop_graph(b);
+    for (int s = 0; s < n; ++s) b->ty[s] = rows[s];
+    std::vector<char> all(n, 1);
+    return plan(b, 0, all, &b->total);
+}
+
 harm_status harm_batch_tune(harm_batch *b, void *const *iq)
 {
     if (!b) return fail(HARM_E_INVALID, "batch is NULL");

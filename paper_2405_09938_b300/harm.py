@@ -90,6 +90,7 @@ SIGNATURES = {
     "harm_batch_create": (C.c_int, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP)]),
     "harm_batch_tune": (C.c_int, [_VP, C.POINTER(_VP)]),
     "harm_batch_tile_rows": (C.c_int, [_VP, C.POINTER(C.c_int32)]),
+    "harm_batch_set_tile_rows": (C.c_int, [_VP, C.POINTER(C.c_int32)]),
     "harm_batch_run": (C.c_int, [_VP, C.POINTER(_VP), C.c_int32]),
     "harm_batch_destroy": (C.c_int, [_VP]),
     "harm_batch_run_noalloc": (C.c_int, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP), C.c_int32]),
@@ -369,6 +370,11 @@ def harm_batch_tile_rows(batch: Batch):
     rows = (C.c_int32 * len(batch.scenes))()
     _check(load_library().harm_batch_tile_rows(batch.handle, rows))
     return [int(v) for v in rows]
+
+
+def harm_batch_set_tile_rows(batch: Batch, rows):
+    arr = (C.c_int32 * len(batch.scenes))(*[int(r) for r in rows])
+    _check(load_library().harm_batch_set_tile_rows(batch.handle, arr))
 
 
 def harm_batch_run(batch: Batch, iqs, zero_first: bool = True):

@@ -104,6 +104,35 @@ def test_batch_tune_and_graph_replay():
         s.close()
 
 
+def test_batch_eight_row_tiles():
+    # 8-row tiles (one facet per thread) pinned on every scene: same echo as the
+    # single-scene accumulator (16-row tiles) and as the oracle
+    import torch
+    descs = _uneven_scenes()
+    scenes = [harm.harm_scene_create(d, harm.HARM_PREC_MIXED) for d in descs]
+    b = harm.harm_batch_create(scenes)
+    with pytest.raises(harm.HarmError):
+        harm.harm_batch_set_tile_rows(b, [8, 12, 8, 8, 8])
+    harm.harm_batch_set_tile_rows(b, [8] * len(descs))
+    assert harm.harm_batch_tile_rows(b) == [8] * len(descs)
+    iqs = _batch_outputs(descs)
+    harm.harm_batch_run(b, iqs)
+    torch.cuda.synchronize()
+    for d, t in zip(descs, iqs):
+        assert rel_rms(t.cpu().numpy(), _single(d)) < 1e-5
+    d = descs[3]
+    pulses = [0, d["n_pulses"] - 1]
+    assert rel_rms(iqs[3].cpu().numpy()[:, pulses, :], oracle.echo(d, pulses)) < 1e-4
+    harm.harm_batch_set_tile_rows(b, [16, 8, 16, 8, 16])  # mixed heights, graph captured again
+    harm.harm_batch_run(b, iqs)
+    torch.cuda.synchronize()
+    for d, t in zip(descs, iqs):
+        assert rel_rms(t.cpu().numpy(), _single(d)) < 1e-5
+    b.close()
+    for s in scenes:
+        s.close()
+
+
 def test_batch_rejects_bad_inputs():
     descs = _uneven_scenes()[:2]
     s64 = harm.harm_scene_create(descs[0], harm.HARM_PREC_FP64)
