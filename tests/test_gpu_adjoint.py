@@ -44,14 +44,15 @@ def _perturbed(d, seed=6):
     return t
 
 
-def _gpu_adjoint(d, n0, np_, resid):
+def _gpu_adjoint(d, n0, np_, resid, rdtype=None):
     import torch
+    rdtype = rdtype or torch.complex64
     scene = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
     c = d["cells"]
     s0 = torch.tensor(c["sigma0"], dtype=torch.float64, device="cuda")
     uv = torch.tensor(c["uv"], dtype=torch.float64, device="cuda")
     harm.harm_scene_set_cells(scene, c["ncx"], c["ncy"], c["cell_m"], s0, uv)
-    r = torch.tensor(resid, dtype=torch.complex64, device="cuda")
+    r = torch.tensor(resid, dtype=rdtype, device="cuda")
     gs = torch.zeros_like(s0)
     guv = torch.zeros_like(uv)
     harm.harm_echo_adjoint(scene, n0, np_, r, gs, guv)
@@ -85,6 +86,17 @@ def test_adjoint_three_channels():
     r = oracle.echo(d, pulses) - oracle.echo(_perturbed(d), pulses)
     gs_o, guv_o = oracle.adjoint(d, pulses, r)
     gs_g, guv_g = _gpu_adjoint(d, 0, 40, r)
+    assert np.abs(gs_g - gs_o).max() <= TOL_GRAD * np.abs(gs_o).max()
+    assert np.abs(guv_g - guv_o).max() <= TOL_GRAD * np.abs(guv_o).max()
+
+
+def test_adjoint_complex128_residual():
+    import torch
+    d = _scene(n_pulses=24, nx=64, ny=48)
+    pulses = list(range(24))
+    r = oracle.echo(d, pulses) - oracle.echo(_perturbed(d), pulses)
+    gs_o, guv_o = oracle.adjoint(d, pulses, r)
+    gs_g, guv_g = _gpu_adjoint(d, 0, 24, r, torch.complex128)
     assert np.abs(gs_g - gs_o).max() <= TOL_GRAD * np.abs(gs_o).max()
     assert np.abs(guv_g - guv_o).max() <= TOL_GRAD * np.abs(guv_o).max()
 
