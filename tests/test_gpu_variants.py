@@ -57,6 +57,16 @@ def test_variant_mixed_matches_oracle(name):
     _check(VARIANTS[name](_base()), harm.HARM_PREC_MIXED, TOL_MIXED)
 
 
+@pytest.mark.parametrize("name", ["uv_grids", "cwm", "all"])
+def test_variant_mixed_three_channels(name):
+    # one receive antenna: the variant kernels' general channel loop (six-channel
+    # scenes run instantiations with a compile-time channel count)
+    d = _base()
+    tx, rx = hs.geometry(d["n_pulses"], ("A",), (-hs.PHASE_CENTRE_SPACING_M, 0.0, hs.PHASE_CENTRE_SPACING_M))
+    d["tx"], d["rx"] = tx, rx
+    _check(VARIANTS[name](d), harm.HARM_PREC_MIXED, TOL_MIXED)
+
+
 @pytest.mark.parametrize("name", list(VARIANTS))
 def test_variant_fp64_matches_oracle(name):
     d = VARIANTS[name](_base(n_pulses=48))
