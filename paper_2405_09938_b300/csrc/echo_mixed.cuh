@@ -850,10 +850,19 @@ struct FacetGeo {
 template <typename OutT>
 struct ScatterSink {
     float *stage;
-    float2 *tiles;  // [kTileBufs][nc][WT]
+    float2 *tiles;    // [kTileBufs][nc][WT]
     OutT *iq;
-    int n, n0, np, buf;
+    int n0, np;
+    size_t cstride;   // elements between channels of the IQ
+    float2 *tiles_p;  // the current pulse's range tiles, [nc][WT]
+    OutT *iq_p;       // the current pulse's IQ row of channel 0
     PairPlan plan;
+    // per-pulse bases, so that a channel adds one offset to each
+    __device__ __forceinline__ void set_pulse(const MixedArgs &A, int n, int buf)
+    {
+        tiles_p = tiles + buf * A.S.nc * WT;
+        iq_p = iq + 2 * (size_t)(n - n0) * A.S.nr;
+    }
     // the bins of the channel's two facets are known: plan the warp window
     __device__ __forceinline__ void prepare(int kba, int kbb, bool va, bool vb) { plan = plan_pair(kba, kbb, va, vb); }
     // the two facets' taps and values: one warp reduction for both, or one each
@@ -863,9 +872,9 @@ struct ScatterSink {
                                          bool vb)
     {
         if (plan.kmin == INT_MAX) return;
-        float2 *tile_c = tiles + (buf * A.S.nc + ch) * WT;
+        float2 *tile_c = tiles_p + ch * WT;
         const int tile_base = kbase - WT_LO;
-        OutT *grow = iq + 2 * ((size_t)ch * np + (n - n0)) * A.S.nr;
+        OutT *grow = iq_p + ch * cstride;
         if (plan.ok) {
             warp_scatter_pair<OutT>(plan, stage, tile_c, tile_base, kba, kbb, va, vb, ha, hb, vre, vim, A.S.nr, grow,
                                     A.S.flags);
@@ -1360,6 +1369,7 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
     sink.iq = iq;
     sink.n0 = n0;
     sink.np = np;
+    sink.cstride = 2 * (size_t)np * S.nr;
     // pack the two facets: .x = row w, .y = row w + 8 (a copy of .x, masked off, for 8-row tiles)
     PairGeo G;
     const FacetGeo &gq = two ? gb : ga;
@@ -1393,8 +1403,7 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
             G.zi = make_float2(ga.z.y, two ? gb.z.y : 0.0f);
             for (; n < ne; ++n) {
                 const int pi = n - c0;
-                sink.n = n;
-                sink.buf = n & (kTileBufs - 1);
+                sink.set_pulse(A, n, n & (kTileBufs - 1));
                 float2 st[NF];
                 eval_state<NF>(sm, C, sm.pr[pi].tau, st);
                 facet_pulse2<TAPS, V, Var<V>::FWD_CU, NCC>(sm, A, P, G, st, pi, xi_x, fi, sink);
