@@ -5,9 +5,12 @@
 // Work decomposition (one CTA = a 32 x 16 facet tile x a 128-pulse batch):
 //  1. Facet generator: the surface of the tile over the batch is expanded in time
 //     about the batch centre, eta(t_c + tau) = sum_m eta_m tau^m (m <= 5), with
-//     the Taylor coefficients eta_m = Re sum_w Q_w E_{w,m} accumulated over the
-//     wave components (register-blocked FP32 contraction, separable phasors Q).
-//  2. FP64 tile references, per 32-pulse chunk: for every pulse and antenna, the
+//     the Taylor coefficients accumulated over the wave components: each is a
+//     real factor times the real or imaginary part of the component's phasor
+//     Q_w = e^{i kx x} a e^{i (ky y + phi)} e^{-i omega t_c} (FP32, packed over
+//     pairs of orders; 64-component chunks of the factors and of the tile's
+//     column and row phasors staged in shared memory).
+//  2. FP64 tile references, per 16-pulse chunk: for every pulse and antenna, the
 //     range R from the antenna to the tile's reference point on the mean surface,
 //     its unit vector and the tile's reduced reference phase and range-bin offset.
 //     Per facet, r - R is a small offset that FP32 carries to ~1e-8 m:
