@@ -159,8 +159,9 @@ struct PolyArgs {
     float2 sinc2[kSincDeg + 1];
 };
 
-// Bytes of one generator chunk in shared memory: the time tables of WCH wave
-// components (order pairs) and their phasors on the tile's columns and rows.
+// Bytes of one generator chunk in shared memory: the real Taylor factors of WCH
+// wave components (nf fields x kOrders orders, float) and their phasors on the
+// tile's TX columns and TY rows (float2).
 __host__ __device__ constexpr int wave_chunk_bytes(int nf) { return WCH * (nf * kOrders * 4 + (TX + TY) * 8); }
 
 // Shared-memory layout (bytes), sized for nc channels and nf state fields.
@@ -504,9 +505,11 @@ __device__ __forceinline__ float het_weight(const DevScene &S, int cx, int cy, i
 }
 
 // Taylor coefficients in time of the NF state fields of two facets (column ix,
-// rows iya / iyb), accumulated over the wave components of every wave set in R
-// (weighted per facet by Eq. 2 for a heterogeneous sea state), the time tables
-// staged in shared-memory chunks.
+// rows iya / iyb of the tile at (tx0, ty0)), accumulated over the wave components
+// of every wave set in R (weighted per facet by Eq. 2 for a heterogeneous sea
+// state). Per chunk of WCH components the real Taylor factors and the tile's
+// column and row phasors (the rows times e^{-i omega t_c}) are staged in shared
+// memory; each coefficient pair (orders 2p, 2p + 1) takes one FFMA2 per facet.
 template <int NF, bool HET, int UNROLL>
 __device__ void taylor_coeffs(const Smem &sm, const MixedArgs &A, int batch, int tx0, int ty0, int ix, int iya,
                               int iyb, const SetRange &R, float2 C[NF][kOrders])
