@@ -78,6 +78,8 @@ int batch_tiles(const harm_scene *s, int ty)
 
 int batch_variant(const harm_scene *s) { return mixed_variant(s->dev); }
 
+bool batch_share3(const harm_scene *s) { return s->dev.nc == 6 && s->dev.rx_share == 0x36u; }
+
 int batch_ctas(int device, int variant)
 {
     int sms = 0;

@@ -1027,7 +1027,7 @@ __device__ __forceinline__ void pair_gain(const Smem &sm, const DevScene &S, con
 // their rest positions moved by the horizontal displacement, their normal is the
 // cross product of the displaced surface's tangents and their area scales with
 // its vertical component; with u-v grids the pattern gains are complex.
-template <int TAPS, int V, int CU, int NCC, typename Sink>
+template <int TAPS, int V, int CU, int NCC, bool SH3, typename Sink>
 __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A, const PolyArgs &P, const PairGeo &G,
                                              const float2 fs[Var<V>::NF], int pi, float xi_x, float fi,
                                              Sink &sink)
@@ -1110,7 +1110,7 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
             const float2 ur = mul2(add2(R.u0, fma2(X0, R.aRx, fma2(X1, R.aRy, mul2(eta, R.aRz)))), rho_r);
             const float2 vr = mul2(add2(R.v0, fma2(X0, R.eRx, fma2(X1, R.eRy, mul2(eta, R.eRz)))), rho_r);
             pair_gain(sm, S, P, 1 + ch, A.rx_laz_l[ch], A.rx_lel_l[ch], ur, vr, gr, gri);
-        } else if ((S.rx_share >> ch) & 1u) {
+        } else if (SH3 ? (ch % 3 != 0) : ((S.rx_share >> ch) & 1u)) {
             // phase centre of the same receive antenna as channel ch - 1: same gain
             gr = gr_prev;
         } else {
@@ -1124,7 +1124,7 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
         const float2 qz = neg2(fma2(fma2(eta, R.invR, R.uz), rho_r, rt2));
         // sqrt(sigma0 A) = X rsqrt(X Q_z), X = base A (1 + m cos phi) max(0, n.Q) / |n| (x n_z with the CWM)
         float2 amp_s = G.amp_static;
-        if ((S.rx_share >> ch) & 1u) {
+        if (SH3 ? (ch % 3 != 0) : ((S.rx_share >> ch) & 1u)) {
             // phase centre of the previous channel's antenna: its Q direction differs
             // by ~(separation / R) ~ 6e-6 rad, the NRCS by < 4e-6 relative
             amp_s = amps_prev;
@@ -1338,7 +1338,7 @@ __device__ __forceinline__ void eval_state(const Smem &sm, const float2 C[NF][kO
 
 // One forward work item (tile x pulse batch) of one scene. Every thread of the
 // CTA calls it; it starts and ends with the CTA's range tiles all zero.
-template <int TAPS, typename OutT, int V, int NCC = 0>
+template <int TAPS, typename OutT, int V, int NCC = 0, bool SH3 = false>
 __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs &P, const ItemGeo &I, int n0, int np,
                              OutT *iq)
 {
@@ -1412,7 +1412,7 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
                 sink.set_pulse(A, n, n & (kTileBufs - 1));
                 float2 st[NF];
                 eval_state<NF>(sm, C, sm.pr[pi].tau, st);
-                facet_pulse2<TAPS, V, Var<V>::FWD_CU, NCC>(sm, A, P, G, st, pi, xi_x, fi, sink);
+                facet_pulse2<TAPS, V, (SH3 ? 3 : Var<V>::FWD_CU), NCC, SH3>(sm, A, P, G, st, pi, xi_x, fi, sink);
                 // flush the range tiles of pulse pairs (one barrier per two pulses;
                 // a tile is reused four pulses later, after at least one more barrier)
                 if ((pi & 1) || n == ce - 1) {
@@ -1444,7 +1444,7 @@ __device__ __forceinline__ void clear_smem(const Smem &sm, int nc)
     for (int i = threadIdx.x; i < NWARP * SBINS * SROW; i += NT) sm.stage[i] = 0.0f;
 }
 
-template <int TAPS, typename OutT, int V, int NCC>
+template <int TAPS, typename OutT, int V, int NCC, bool SH3>
 __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     accumulate_mixed_kernel(MixedArgs A, PolyArgs P, int n0, int np, int b0, int ty, OutT *iq)
 {
@@ -1453,7 +1453,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     const ItemGeo I = item_geo(A, blockIdx.x, b0 + blockIdx.y, ty, n0, np);
     if (I.pa >= I.pe) return;
     clear_smem(sm, A.S.nc);
-    forward_item<TAPS, OutT, V, NCC>(sm, A, P, I, n0, np, iq);
+    forward_item<TAPS, OutT, V, NCC, SH3>(sm, A, P, I, n0, np, iq);
 }
 
 // Work list of a batched launch: scene s owns items [start[s], start[s + 1]);
@@ -1473,7 +1473,7 @@ struct BatchItems {
 // Persistent batched forward launch: a fixed pool of CTAs pulls work items from
 // a global counter until the list is exhausted (no waiting on other CTAs). The
 // scene arguments of the current item are copied to shared memory.
-template <int TAPS, int V, int NCC>
+template <int TAPS, int V, int NCC, bool SH3 = false>
 __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     batch_mixed_kernel(BatchItems B, PolyArgs P, unsigned int *counter)
 {
@@ -1517,7 +1517,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
         const int local = it - B.start[k];
         const int tiles = B.tiles[scene];
         const ItemGeo I = item_geo(args, local % tiles, local / tiles, B.ty[scene], 0, args.S.np_total);
-        if (I.pa < I.pe) forward_item<TAPS, float, V, NCC>(sm, args, P, I, 0, args.S.np_total, B.iq[scene]);
+        if (I.pa < I.pe) forward_item<TAPS, float, V, NCC, SH3>(sm, args, P, I, 0, args.S.np_total, B.iq[scene]);
         __syncthreads();
     }
 }
@@ -1558,7 +1558,7 @@ __device__ __forceinline__ void add_cell_grads(const FacetGeo &G, float as, floa
     }
 }
 
-template <int TAPS, typename InT, int V, int NCC>
+template <int TAPS, typename InT, int V, int NCC, bool SH3>
 __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     adjoint_mixed_kernel(MixedArgs A, PolyArgs P, int n0, int np, int b0, const InT *resid, double *g_sigma,
                          double *g_uv)
@@ -1646,7 +1646,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
                 sink.n = n;
                 float2 st[NF];
                 eval_state<NF>(sm, C, sm.pr[pi].tau, st);
-                facet_pulse2<TAPS, V, (NCC > 0 ? NCC : 1), NCC>(sm, A, P, G, st, pi, xi_x, fi, sink);
+                facet_pulse2<TAPS, V, (NCC > 0 ? NCC : 1), NCC, SH3>(sm, A, P, G, st, pi, xi_x, fi, sink);
             }
         }
     }
@@ -1768,16 +1768,16 @@ cudaError_t over_batches(const DevScene &S, const MixedTables &M, int ty, int n0
     return cudaSuccess;
 }
 
-template <int TAPS, typename OutT, int V, int NCC>
+template <int TAPS, typename OutT, int V, int NCC, bool SH3 = false>
 cudaError_t accumulate_nc(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, OutT *iq)
 {
     const MixedArgs A = make_args(S, M);
     const PolyArgs P = make_poly(M);
     const int bytes = layout(S.nc, true, Var<V>::NF).total;
-    cudaError_t e = prep(accumulate_mixed_kernel<TAPS, OutT, V, NCC>, bytes);
+    cudaError_t e = prep(accumulate_mixed_kernel<TAPS, OutT, V, NCC, SH3>, bytes);
     if (e != cudaSuccess) return e;
     return over_batches(S, M, TY, n0, np, [&](int bb, dim3 grid) {
-        accumulate_mixed_kernel<TAPS, OutT, V, NCC><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, TY, iq);
+        accumulate_mixed_kernel<TAPS, OutT, V, NCC, SH3><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, TY, iq);
         return cudaGetLastError();
     });
 }
@@ -1788,22 +1788,24 @@ cudaError_t accumulate_nc(const DevScene &S, const MixedTables &M, cudaStream_t 
 template <int TAPS, typename OutT, int V>
 cudaError_t accumulate_t(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, OutT *iq)
 {
-    if constexpr (TAPS == 8)
+    if constexpr (TAPS == 8) {
+        if (S.nc == 6 && S.rx_share == 0x36u) return accumulate_nc<TAPS, OutT, V, 6, true>(S, M, st, n0, np, iq);
         if (S.nc == 6) return accumulate_nc<TAPS, OutT, V, 6>(S, M, st, n0, np, iq);
+    }
     return accumulate_nc<TAPS, OutT, V, 0>(S, M, st, n0, np, iq);
 }
 
-template <int TAPS, typename InT, int V, int NCC>
+template <int TAPS, typename InT, int V, int NCC, bool SH3 = false>
 cudaError_t adjoint_nc(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, const InT *resid,
                        double *g_sigma, double *g_uv)
 {
     const MixedArgs A = make_args(S, M);
     const PolyArgs P = make_poly(M);
     const int bytes = layout(S.nc, true, Var<V>::NF).total;
-    cudaError_t e = prep(adjoint_mixed_kernel<TAPS, InT, V, NCC>, bytes);
+    cudaError_t e = prep(adjoint_mixed_kernel<TAPS, InT, V, NCC, SH3>, bytes);
     if (e != cudaSuccess) return e;
     return over_batches(S, M, TY, n0, np, [&](int bb, dim3 grid) {
-        adjoint_mixed_kernel<TAPS, InT, V, NCC><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, resid, g_sigma, g_uv);
+        adjoint_mixed_kernel<TAPS, InT, V, NCC, SH3><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, resid, g_sigma, g_uv);
         return cudaGetLastError();
     });
 }
@@ -1814,8 +1816,10 @@ template <int TAPS, typename InT, int V>
 cudaError_t adjoint_t(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, const InT *resid,
                       double *g_sigma, double *g_uv)
 {
-    if constexpr (TAPS == 8)
+    if constexpr (TAPS == 8) {
+        if (S.nc == 6 && S.rx_share == 0x36u) return adjoint_nc<TAPS, InT, V, 6, true>(S, M, st, n0, np, resid, g_sigma, g_uv);
         if (S.nc == 6) return adjoint_nc<TAPS, InT, V, 6>(S, M, st, n0, np, resid, g_sigma, g_uv);
+    }
     return adjoint_nc<TAPS, InT, V, 0>(S, M, st, n0, np, resid, g_sigma, g_uv);
 }
 
@@ -1874,7 +1878,10 @@ struct MixedLaunch {
         if (L.taps == 1) {
             if ((e = prep(batch_mixed_kernel<1, V, 0>, bytes)) != cudaSuccess) return e;
             batch_mixed_kernel<1, V, 0><<<L.ctas, NT, bytes, st>>>(B, P, L.counter);
-        } else if (L.nc == 6) {  // compile-time channel count, as for single scenes
+        } else if (L.nc == 6 && L.share3) {  // compile-time channel layout, as for single scenes
+            if ((e = prep(batch_mixed_kernel<8, V, 6, true>, bytes)) != cudaSuccess) return e;
+            batch_mixed_kernel<8, V, 6, true><<<L.ctas, NT, bytes, st>>>(B, P, L.counter);
+        } else if (L.nc == 6) {
             if ((e = prep(batch_mixed_kernel<8, V, 6>, bytes)) != cudaSuccess) return e;
             batch_mixed_kernel<8, V, 6><<<L.ctas, NT, bytes, st>>>(B, P, L.counter);
         } else {

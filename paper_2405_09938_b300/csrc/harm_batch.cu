@@ -24,6 +24,7 @@ struct harm_batch {
     int device = 0;
     int nc = 0, taps = 8;
     int variant = 0;
+    int share3 = 0;
     int ctas = 0;
     std::vector<int> ty;        // tile rows by scene
     std::vector<int> order;     // processing order (largest first)
@@ -128,6 +129,7 @@ harm::BatchLaunch launch_desc(harm_batch *b, int total)
     L.taps = b->taps;
     L.ctas = b->ctas;
     L.variant = b->variant;
+    L.share3 = b->share3;
     return L;
 }
 
@@ -200,6 +202,9 @@ harm_status harm_batch_create(harm_scene *const *scenes, int32_t n, harm_batch *
     b->nc = scenes[0]->desc.n_channels;
     b->taps = scenes[0]->desc.taps;
     b->variant = harm::batch_variant(scenes[0]);
+    b->share3 = 1;
+    for (int s = 0; s < n; ++s)
+        if (!harm::batch_share3(scenes[s])) b->share3 = 0;
     b->ctas = harm::batch_ctas(b->device, b->variant);
     b->ty.assign(n, 16);
     b->order.resize(n);

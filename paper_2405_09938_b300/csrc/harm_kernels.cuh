@@ -105,11 +105,13 @@ struct BatchLaunch {
     const MixedTables *poly; // tap / sinc polynomials (shared)
     int n, total, nc, taps, ctas;
     int variant;             // per-pulse code variant shared by the scenes (see batch_variant)
+    int share3;              // every scene: 6 channels, two receive antennas of 3 phase centres
 };
 size_t batch_args_bytes();
 void batch_fill_args(const harm_scene *s, void *dst);
 int batch_tiles(const harm_scene *s, int ty);
 int batch_variant(const harm_scene *s);  // surface model / pattern kind of the per-pulse code
+bool batch_share3(const harm_scene *s);  // 6 channels in two antennas of 3 phase centres
 int batch_ctas(int device, int variant);
 cudaError_t batch_launch(const BatchLaunch &L, cudaStream_t st);
 

@@ -155,6 +155,9 @@ extern "C" harm_status harm_batch_run_noalloc(harm_scene *const *scenes, int32_t
         L.nc = scenes[0]->desc.n_channels;
         L.taps = scenes[0]->desc.taps;
         L.variant = harm::batch_variant(scenes[0]);
+        L.share3 = 1;
+        for (int s = 0; s < n; ++s)
+            if (!harm::batch_share3(scenes[s])) L.share3 = 0;
         L.ctas = harm::batch_ctas(dev, L.variant);
         e = harm::batch_launch(L, stream);
     }
