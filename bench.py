@@ -129,20 +129,20 @@ ALGO_FLOPS_ACCUMULATOR = 150.0
 ALGO_FLOPS_GENERATOR_PER_FACET_PULSE = 3072.0
 # What the kernel executes per contribution, from the instruction-mix counters on
 # the 512-pulse capture of the headline scene (FFMA2 = 4 flops, FFMA / FMUL2 /
-# FADD2 = 2, FMUL / FADD = 1; per contribution 38.8 FFMA2 + 9.9 FFMA + 11.0 FMUL2
+# FADD2 = 2, FMUL / FADD = 1; per contribution 38.4 FFMA2 + 9.9 FFMA + 10.6 FMUL2
 # + 11.8 FMUL + 9.2 FADD2 + 1.5 FADD): the time-Taylor generator replaces the
 # direct synthesis, so this is far below the algorithmic count.
-EXECUTED_FLOPS_PER_CONTRIBUTION = 228.6
+EXECUTED_FLOPS_PER_CONTRIBUTION = 226.3
 # All instructions issued per contribution (thread level, same capture).
-INSTR_PER_CONTRIBUTION = 213.8
+INSTR_PER_CONTRIBUTION = 200.8
 # DRAM bytes (read + write) of one headline launch (2048 pulses), from one ncu
 # capture of dram__bytes_read.sum + dram__bytes_write.sum, and the SHA-256 of the
 # kernel sources' code (comments and blank lines dropped) it was taken on: the
 # figure is reported only while they match.
-TRAFFIC_BYTES = 81036800 + 27006976
+TRAFFIC_BYTES = 80862208 + 27419392
 TRAFFIC_PULSES = 2048
 TRAFFIC_SOURCES = ("echo_mixed.cuh", "harm_kernels.cuh", "harm_internal.cuh")
-TRAFFIC_SHA256 = "4a6aef9b3e675672066664e1c8411b8eec68bb37398463e83faacdbfdf905f02"
+TRAFFIC_SHA256 = "a551b934c461309b0906b7bf82bd07f08f03b10c10f308e102f6b007276d8ce3"
 
 
 def _code_lines(raw):
@@ -377,8 +377,10 @@ def main():
                      "traffic": captured_traffic(np_step) if prec == harm.HARM_PREC_MIXED else None,
                      "kernel": "accumulate_mixed_kernel" if prec == harm.HARM_PREC_MIXED else "accumulate_f64_kernel",
                      "kernel_ms": kern_ms, "flops_per_contribution": algo_per_unit,
-                     "flops_basis": "algorithmic: %.0f accumulator + %.0f / %d channels generator (direct "
-                                    "256-component synthesis) per contribution" % (
+                     "flops_basis": "algorithmic: %.0f accumulator (Rx pattern and NRCS counted per channel; "
+                                    "the kernel evaluates them once per receive antenna and shares them between "
+                                    "its phase centres, hence frac slightly above 1) + %.0f / %d channels "
+                                    "generator (direct 256-component synthesis) per contribution" % (
                                         ALGO_FLOPS_ACCUMULATOR, ALGO_FLOPS_GENERATOR_PER_FACET_PULSE, nc),
                      "peak_basis": "148 SM x 128 FP32 lanes x 2 x %.0f MHz (max SM clock)" % sm_max,
                      "executed_flops_per_contribution": EXECUTED_FLOPS_PER_CONTRIBUTION,
