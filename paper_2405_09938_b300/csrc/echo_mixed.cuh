@@ -1412,7 +1412,7 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
                 sink.set_pulse(A, n, n & (kTileBufs - 1));
                 float2 st[NF];
                 eval_state<NF>(sm, C, sm.pr[pi].tau, st);
-                facet_pulse2<TAPS, V, (SH3 ? 3 : Var<V>::FWD_CU), NCC, SH3>(sm, A, P, G, st, pi, xi_x, fi, sink);
+                facet_pulse2<TAPS, V, (SH3 ? 6 : Var<V>::FWD_CU), NCC, SH3>(sm, A, P, G, st, pi, xi_x, fi, sink);
                 // flush the range tiles of pulse pairs (one barrier per two pulses;
                 // a tile is reused four pulses later, after at least one more barrier)
                 if ((pi & 1) || n == ce - 1) {
