@@ -79,7 +79,9 @@ struct Var {
     static constexpr int NF = CWM ? 8 : 3;        // state fields
     static constexpr int MIN_BLOCKS = CWM ? 1 : 2; // CTAs per SM the registers allow
     // channel-loop unroll of the forward pulse body (measured: 2 for the linear
-    // surface; the Choppy Wave Model, at one CTA per SM, runs best rolled)
+    // surface; the Choppy Wave Model, at one CTA per SM, runs best rolled). With
+    // the six-channel two-antenna layout known at compile time the loop is
+    // unrolled fully (by three, one antenna, for the Choppy Wave Model).
     static constexpr int FWD_CU = CWM ? 1 : 2;
 };
 
@@ -1412,7 +1414,7 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
                 sink.set_pulse(A, n, n & (kTileBufs - 1));
                 float2 st[NF];
                 eval_state<NF>(sm, C, sm.pr[pi].tau, st);
-                facet_pulse2<TAPS, V, (SH3 ? 6 : Var<V>::FWD_CU), NCC, SH3>(sm, A, P, G, st, pi, xi_x, fi, sink);
+                facet_pulse2<TAPS, V, (SH3 ? (Var<V>::CWM ? 3 : 6) : Var<V>::FWD_CU), NCC, SH3>(sm, A, P, G, st, pi, xi_x, fi, sink);
                 // flush the range tiles of pulse pairs (one barrier per two pulses;
                 // a tile is reused four pulses later, after at least one more barrier)
                 if ((pi & 1) || n == ce - 1) {
