@@ -129,3 +129,31 @@ def test_version_1_descriptor_and_variant_validation():
     assert out.value is None
     # pattern setter on a NULL scene
     assert lib.harm_scene_set_pattern(None, -1, 2, 2, 0.0, 1.0, 0.0, 1.0, None) == harm.HARM_E_INVALID
+
+
+def test_binding_rejects_bad_host_and_device_arguments():
+    # argument marshalling checks of the binding run before any library call
+    import torch
+    harm.load_library(harm_build.build())
+
+    class _NoScene:
+        @property
+        def handle(self):
+            raise AssertionError("the scene must not be touched")
+
+    sc = _NoScene()
+    with pytest.raises(harm.HarmError) as e:
+        harm.harm_echo_accumulate_host(sc, 0, 1, "not a tensor")
+    assert e.value.status == harm.HARM_E_INVALID
+    strided = torch.zeros((2, 4, 8), dtype=torch.complex64)[:, ::2, :]
+    with pytest.raises(harm.HarmError) as e:
+        harm.harm_echo_accumulate_host(sc, 0, 2, strided)
+    assert "contiguous" in str(e.value)
+
+
+    class _NullScene:
+        handle = None  # the device-pointer check fails before the library is called
+
+    with pytest.raises(harm.HarmError) as e:
+        harm.harm_echo_accumulate(_NullScene(), 0, 1, torch.zeros(4, dtype=torch.complex64))  # a CPU tensor
+    assert "CUDA" in str(e.value)
