@@ -132,6 +132,21 @@ def test_sixteen_channels_maximum():
             assert rel_rms(got[c], want[c]) < tol
 
 
+def test_six_channels_without_shared_antennas():
+    # six channels whose phase centres are 100 m apart (more than the 50 m that
+    # makes them one antenna): no pattern / NRCS sharing, the six-channel
+    # instantiation with the sharing mask read at run time
+    pcs = (-100.0, 0.0, 100.0)
+    d = small_wave_scene(n_pulses=40, nx=70, ny=33, n_range=1024)
+    d["tx"], d["rx"] = hs.geometry(40, ("A", "B"), pcs)
+    pulses = [0, 17, 39]
+    want = oracle.echo(d, pulses)
+    got = run_echo(d, harm.HARM_PREC_MIXED, 0, 40, "c64")[:, pulses, :]
+    assert rel_rms(got, want) < TOL_MIXED
+    for c in range(6):
+        assert rel_rms(got[c], want[c]) < TOL_MIXED
+
+
 def test_echo_partly_outside_range_window():
     # a short range window cuts the echo: taps outside [0, n_range) are dropped
     d = small_wave_scene(n_pulses=16, nx=64, ny=64, n_range=1024)
