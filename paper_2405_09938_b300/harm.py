@@ -117,6 +117,7 @@ def load_library(path: str = LIB_PATH):
 
 
 def harm_last_error() -> str:
+    """Message of the last non-OK status on this thread ("" if none)."""
     return load_library().harm_last_error().decode()
 
 
@@ -217,6 +218,9 @@ class Scene:
 
 
 def harm_scene_create(desc: dict, precision: int = HARM_PREC_FP64, stream=None) -> Scene:
+    """Create a scene on the current device from a scene dictionary (see
+    :mod:`harm_scenes`); `stream` is a torch stream or None (default stream).
+    Raises HarmError for an invalid descriptor."""
     lib = load_library()
     s, keep = make_desc(desc, precision)
     out = C.c_void_p()
@@ -248,10 +252,13 @@ def harm_scene_set_pattern(scene: Scene, antenna: int, pattern):
 
 
 def harm_scene_destroy(scene: Scene):
+    """Release the scene after its stream has drained."""
     scene.close()
 
 
 def harm_scene_query(scene: Scene) -> dict:
+    """Sizes of the scene: facets, pulses, range samples, channels, waves,
+    precision, pulses per work item, range bin and per-channel range starts."""
     info = harm_scene_info()
     _check(load_library().harm_scene_query(scene.handle, C.byref(info)))
     return {"n_facets": info.n_facets, "n_pulses": info.n_pulses, "n_range": info.n_range,
@@ -270,6 +277,9 @@ def _dev_ptr(t, what):
 
 
 def harm_scene_set_cells(scene: Scene, ncx, ncy, cell_m, sigma0=None, uv=None):
+    """Per-cell NRCS base (float64 CUDA tensor [ncy, ncx]) and current
+    ([ncy, ncx, 2]) on cells of cell_m metres; either may be None. The tensors are
+    kept alive with the scene."""
     sp = _dev_ptr(sigma0, "sigma0") if sigma0 is not None else None
     up = _dev_ptr(uv, "uv") if uv is not None else None
     _check(load_library().harm_scene_set_cells(scene.handle, ncx, ncy, cell_m, sp, up))
@@ -277,6 +287,9 @@ def harm_scene_set_cells(scene: Scene, ncx, ncy, cell_m, sigma0=None, uv=None):
 
 
 def harm_facets_generate(scene: Scene, n0: int, np_: int, state):
+    """Facet states of pulses [n0, n0 + np_) into `state`, a CUDA tensor
+    [np_][F][n_facets] (float64 for FP64 scenes, float32 for mixed; F = 3, or 8
+    with the Choppy Wave Model)."""
     _check(load_library().harm_facets_generate(scene.handle, n0, np_, _dev_ptr(state, "state")))
 
 
@@ -290,6 +303,9 @@ def _dtype_code(t):
 
 
 def harm_echo_accumulate(scene: Scene, n0: int, np_: int, iq, zero_first: bool = True):
+    """Add the echo of pulses [n0, n0 + np_) into `iq`, a contiguous CUDA tensor
+    [n_channels][np_][n_range] (complex64 or complex128), cleared first unless
+    zero_first is False. Asynchronous on the scene's stream."""
     _check(load_library().harm_echo_accumulate(scene.handle, n0, np_, _dev_ptr(iq, "iq"),
                                                _dtype_code(iq), 1 if zero_first else 0))
 
@@ -308,6 +324,9 @@ def harm_echo_accumulate_host(scene: Scene, n0: int, np_: int, iq_host, block_pu
 
 
 def harm_echo_adjoint(scene: Scene, n0: int, np_: int, resid, grad_sigma0=None, grad_uv=None):
+    """Add the gradients of sum |IQ - target|^2 for the residual `resid` (IQ -
+    target, same layout and dtype as the IQ) to grad_sigma0 [ncy, ncx] and grad_uv
+    [ncy, ncx, 2] (float64 CUDA tensors, either may be None). Needs cells."""
     gs = _dev_ptr(grad_sigma0, "grad_sigma0") if grad_sigma0 is not None else None
     gu = _dev_ptr(grad_uv, "grad_uv") if grad_uv is not None else None
     _check(load_library().harm_echo_adjoint(scene.handle, n0, np_, _dev_ptr(resid, "resid"),
@@ -315,6 +334,7 @@ def harm_echo_adjoint(scene: Scene, n0: int, np_: int, resid, grad_sigma0=None, 
 
 
 def harm_scene_sync(scene: Scene):
+    """Wait for the scene's stream; raises HarmError for device-side errors."""
     _check(load_library().harm_scene_sync(scene.handle))
 
 
@@ -356,6 +376,8 @@ def _ptr_array(tensors, what):
 
 
 def harm_batch_create(scenes) -> Batch:
+    """Group mixed-precision scenes (same device, channels and taps) into one
+    persistent batched launch."""
     arr = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
     out = C.c_void_p()
     _check(load_library().harm_batch_create(arr, len(scenes), C.byref(out)))
@@ -363,25 +385,32 @@ def harm_batch_create(scenes) -> Batch:
 
 
 def harm_batch_tune(batch: Batch, iqs):
+    """Time 8- and 16-row tiles per scene-size class and keep the faster;
+    overwrites the complex64 CUDA tensors `iqs` (one per scene). Synchronous."""
     _check(load_library().harm_batch_tune(batch.handle, _ptr_array(iqs, "iq")))
 
 
 def harm_batch_tile_rows(batch: Batch):
+    """Tile height (8 or 16 facet rows) of each scene."""
     rows = (C.c_int32 * len(batch.scenes))()
     _check(load_library().harm_batch_tile_rows(batch.handle, rows))
     return [int(v) for v in rows]
 
 
 def harm_batch_set_tile_rows(batch: Batch, rows):
+    """Pin the tile height (8 or 16) of each scene instead of tuning."""
     arr = (C.c_int32 * len(batch.scenes))(*[int(r) for r in rows])
     _check(load_library().harm_batch_set_tile_rows(batch.handle, arr))
 
 
 def harm_batch_run(batch: Batch, iqs, zero_first: bool = True):
+    """Echo of every scene over its burst into `iqs` (complex64 CUDA tensors, one
+    per scene), replayed from a CUDA graph."""
     _check(load_library().harm_batch_run(batch.handle, _ptr_array(iqs, "iq"), 1 if zero_first else 0))
 
 
 def harm_batch_destroy(batch: Batch):
+    """Release the batch (its scenes stay valid)."""
     batch.close()
 
 
