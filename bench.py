@@ -139,10 +139,10 @@ INSTR_PER_CONTRIBUTION = 191.7
 # capture of dram__bytes_read.sum + dram__bytes_write.sum, and the SHA-256 of the
 # kernel sources' code (comments and blank lines dropped) it was taken on: the
 # figure is reported only while they match.
-TRAFFIC_BYTES = 81125888 + 27682048
+TRAFFIC_BYTES = 80799232 + 27664640
 TRAFFIC_PULSES = 2048
 TRAFFIC_SOURCES = ("echo_mixed.cuh", "harm_kernels.cuh", "harm_internal.cuh")
-TRAFFIC_SHA256 = "1a6ef0c5267d0394a0a0483aa536e22ce022dedf4c0a428da92689e5c710b3ec"
+TRAFFIC_SHA256 = "3a65f113ca8efad65665c911ec8c7cfdc9e0442b812166f08b0c6b24d617bed8"
 
 
 def _code_lines(raw):

@@ -282,15 +282,6 @@ __device__ __forceinline__ double wrap_pi(double a)
     return a - 2.0 * kPi * rint(a * (0.5 / kPi));
 }
 
-// Reduce an FP32 phase to [-pi, pi] with a two-part 2 pi (Cody-Waite).
-__device__ __forceinline__ float reduce_phase(float a)
-{
-    float k = rintf(a * 0.15915494309189535f);
-    a = fmaf(-k, 6.28125f, a);
-    a = fmaf(-k, 1.9353071795864769e-3f, a);
-    return a;
-}
-
 // FP64 tile reference of one antenna (state A) for the tile reference point
 // X = (xr, yr, 0): D = X - p, R = |D|, u = D / R, and the stable offset
 // R - |p| = (|X|^2 - 2 p.X) / (R + |p|).
