@@ -194,7 +194,8 @@ harm_status harm_echo_accumulate(harm_scene *scene, int32_t n0, int32_t np, void
    is computed): writes the IQ of pulses [n0, n0 + np) to iq_host, laid out
    [n_channels][np][n_range] complex of `dtype` (overwritten, not added to). The
    burst runs in blocks of block_pulses pulses (<= 0: about an eighth of the
-   burst, a multiple of 128 pulses) into a ring of two device buffers that the
+   burst, a multiple of the mixed path's time-Taylor window of
+   harm_scene_info.pulse_batch = 256 pulses) into a ring of two device buffers that the
    scene owns, alternating between the scene's stream and a second compute
    stream; each block is copied to iq_host on a copy stream while the next one is
    computed. iq_host must be page-locked (cudaHostAlloc / cudaHostRegister)

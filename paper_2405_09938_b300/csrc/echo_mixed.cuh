@@ -2,7 +2,7 @@
 // reference bistatic range and each tile's range offset; FP32 for the per-facet
 // geometry, antenna patterns, NRCS, phase, interpolation taps and accumulation.
 //
-// Work decomposition (one CTA = a 32 x 16 facet tile x a 128-pulse batch):
+// Work decomposition (one CTA = a 32 x 16 facet tile x a 256-pulse batch):
 //  1. Facet generator: the surface of the tile over the batch is expanded in time
 //     about the batch centre, eta(t_c + tau) = sum_m eta_m tau^m (m <= 5), with
 //     the Taylor coefficients accumulated over the wave components: each is a
@@ -60,7 +60,8 @@ constexpr int WA_LO = 14;     // (a 32 x 16 facet tile spans about +-10 bins aro
                               // reference bin, taps and heights included; residuals
                               // outside the window are read from global memory)
 constexpr int NBR = 16;       // pulses per chunk of FP64 tile references
-constexpr int NBG = 128;      // pulses per work item (time-Taylor window of the generator)
+constexpr int NBG = 256;      // pulses per work item (time-Taylor window of the generator;
+                              // |omega tau| <= 0.2 on the headline wave spectrum)
 constexpr int WCH = 64;       // wave components per shared-memory chunk of the generator
 constexpr int SROW = 72;      // floats per bin row of the warp buffer (2 halves of 32 + pad)
 constexpr int SHALF = 36;     // float offset of lanes 16..31 in a row

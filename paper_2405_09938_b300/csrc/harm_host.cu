@@ -25,11 +25,11 @@
 
 namespace harm {
 harm_status set_error(harm_status s, const char *msg);
+int mixed_batch_pulses();
 }
 
 namespace {
 
-constexpr int kBlockQuantum = 128;  // pulses: the generator's time window
 constexpr int kDefaultBlocks = 8;
 
 harm_status fail(harm_status s, const char *fmt, ...)
@@ -59,8 +59,11 @@ harm_status cuda_fail(cudaError_t e, const char *what)
 int block_size(int np, int block_pulses)
 {
     if (block_pulses > 0) return std::min(block_pulses, np);
+    // default blocks are whole time-Taylor windows of the mixed path, so that no
+    // window's generator contraction runs twice
+    const int q = harm::mixed_batch_pulses();
     const int b = (np + kDefaultBlocks - 1) / kDefaultBlocks;
-    return std::min(np, std::max(kBlockQuantum, (b + kBlockQuantum - 1) / kBlockQuantum * kBlockQuantum));
+    return std::min(np, std::max(q, (b + q - 1) / q * q));
 }
 
 // Streams, events and a ring large enough for `bytes` per buffer. A ring that

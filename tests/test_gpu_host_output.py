@@ -62,7 +62,7 @@ def test_host_output_complex128_against_oracle():
     sc = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
     got = _host_echo(sc, d, n0, np_, torch.complex128, 0)
     sc.close()
-    pulses = [0, 127, 128, 255, 256, 299]  # edges of the default 128-pulse blocks and the tail
+    pulses = [0, 127, 128, 255, 256, 299]  # inside and at the edge of the default 256-pulse block, and the tail
     want = oracle.echo(d, pulses)
     err = rel_rms(got[:, pulses, :], want)
     print("host output (complex128) vs oracle: rel RMS %.2e" % err)

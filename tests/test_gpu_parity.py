@@ -107,9 +107,10 @@ def test_mixed_c128_output():
 
 # ------------------------------------------------------------------ edges
 def test_ragged_grid_and_unaligned_pulse_window():
-    # grid not a multiple of the tiles, window crossing batch and epoch edges
-    d = small_wave_scene(n_pulses=120, nx=45, ny=19)
-    n0, np_ = 29, 45
+    # grid not a multiple of the tiles; the pulse window crosses the edge of the
+    # 256-pulse time-Taylor windows (256) and two speckle epoch edges (238, 272)
+    d = small_wave_scene(n_pulses=300, nx=45, ny=19)
+    n0, np_ = 233, 45
     want = oracle.echo(d, list(range(n0, n0 + np_)))
     for prec, tol, dt in ((harm.HARM_PREC_FP64, TOL_FP64, "c128"), (harm.HARM_PREC_MIXED, TOL_MIXED, "c64")):
         got = run_echo(d, prec, n0, np_, dt)

@@ -4,8 +4,8 @@ shift (Eq. 7), u-v antenna gain grids (Sec. III-B), heterogeneous sea states
 (Eq. 1, 2) and the Choppy Wave Model, alone and combined, on both precisions,
 plus the facet generator's CWM fields and the adjoint of a variant scene.
 
-Scenes are 150 x 70 facets (ragged against the 32 x 16 tiles), 200 pulses (two
-128-pulse windows, the second ragged), 6 channels; tolerances as in the base
+Scenes are 150 x 70 facets (ragged against the 32 x 16 tiles), 400 pulses (two
+256-pulse time-Taylor windows, the second ragged), 6 channels; tolerances as in the base
 parity tests: 1e-7 (FP64 path) and 1e-4 (mixed path) IQ relative RMS."""
 import math
 
@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 TOL_FP64 = 1e-7
 TOL_MIXED = 1e-4
-PULSES = [0, 77, 128, 199]
+PULSES = [0, 77, 255, 256, 399]  # both windows, their shared edge and the tail
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -30,7 +30,7 @@ def _cuda():
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
 
 
-def _base(n_pulses=200):
+def _base(n_pulses=400):
     return hs.ati_scene(n_pulses=n_pulses, nx=150, ny=70, n_range=1024)
 
 
@@ -171,7 +171,7 @@ def test_variant_adjoint_matches_oracle_adjoint():
 def test_batch_of_variant_scenes():
     import torch
     descs = []
-    for i, (nx, ny, npul) in enumerate([(90, 40, 96), (64, 70, 130), (40, 33, 50)]):
+    for i, (nx, ny, npul) in enumerate([(90, 40, 96), (64, 70, 270), (40, 33, 50)]):
         d = hs.ati_scene(n_pulses=npul, nx=nx, ny=ny, n_range=1024)
         d["speckle_seed"] = 400 + i
         descs.append(hs.choppy(hs.hetero_sea(hs.ar1_speckle(d, tau_s=0.02, epoch_pulses=8), tile_m=60.0)))
