@@ -172,7 +172,7 @@ harm_status harm_scene_set_cells(harm_scene *scene, int32_t ncx, int32_t ncy, do
 harm_status harm_scene_set_pattern(harm_scene *scene, int32_t antenna, int32_t nu, int32_t nv, double u0, double du,
                                    double v0, double dv, const double *gain_host);
 
-/* Facet generator (Sec. III surface, Sec. IV-B "generate the surface"): writes
+/* Facet generator (Sec. III surface; the per-tile surface synthesis of Sec. IV-B): writes
    the state of every facet for pulses [n0, n0 + np) at the bounce time of each
    pulse, to state_dev laid out [np][F][n_facets], in double for HARM_PREC_FP64
    scenes and in float for HARM_PREC_MIXED scenes. F = 3 fields (eta, eta_x,
