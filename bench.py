@@ -336,7 +336,8 @@ def main():
     for _ in range(e2e_steps):
         ta = time.perf_counter()
         sc = harm.harm_scene_create(desc, prec, stream)
-        h2d = _scene_table_bytes(desc, prec)
+        if not h2d:
+            h2d = _scene_table_bytes(desc, prec, harm.harm_scene_query(sc)["pulse_batch"])
         create_s += time.perf_counter() - ta
         harm.harm_echo_accumulate_host(sc, n0_step, np_step, host_iq)
         harm.harm_scene_sync(sc)
@@ -602,20 +603,26 @@ def _launches_per_step(desc, prec, np_step):
     return max(1, math.ceil(np_step / 65535))
 
 
-def _scene_table_bytes(desc, prec):
-    """Bytes harm_scene_create uploads: pulse and receive states, the wave list
-    (its phasor tables are computed on the device), the Taylor time tables, u-v
-    grid descriptors and the flag words."""
+def _scene_table_bytes(desc, prec, pulse_batch):
+    """Bytes harm_scene_create uploads: pulse states (t, t_s and a 10-double
+    antenna state) and per-channel receive states (antenna state, reduced phase,
+    bin offset); the wave numbers and frequencies (kx, ky, omega, |k|) and the
+    wave list of the phasor-table kernel (5 doubles; the tables themselves are
+    computed on the device) per wave set; u-v grid descriptors and the flag
+    words; for mixed scenes the time-Taylor tables: e^{-i omega t_c} per window
+    of ``pulse_batch`` pulses (complex64), the real factors (float32, fields x 6
+    orders) and the pulse offsets tau (float32)."""
     from paper_2405_09938_b300 import harm
     nw = desc["n_omega"] * desc["n_theta"]
+    het = desc.get("hetero")
+    nsw = nw * (int(np.asarray(het["u10"]).size) if het else 1)
     npul, nc = desc["n_pulses"], len(desc["rx"])
     pulse = npul * (8 * 2 + 8 * 10) + npul * nc * (8 * 10 + 16)
+    waves = nsw * 4 * 8 + nsw * 5 * 8
     if prec == harm.HARM_PREC_MIXED:
         nf = 8 if desc.get("cwm") else 3
-        waves = nw * 40 + math.ceil(npul / 128) * nw * nf * 6 * 8 + npul * 4 + nw * 32
-    else:
-        waves = nw * 40 + nw * 32
-    return pulse + waves + (1 + nc) * 56 + 16
+        waves += math.ceil(npul / pulse_batch) * nsw * 8 + nsw * nf * 6 * 4 + npul * 4
+    return pulse + waves + (1 + nc) * 56 + 4 * 4
 
 
 if __name__ == "__main__":

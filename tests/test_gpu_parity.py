@@ -172,6 +172,20 @@ def test_single_facet_and_single_pulse():
         assert rel_rms(got, want) < tol
 
 
+def test_scene_query_reports_the_scene():
+    d = small_wave_scene(n_pulses=300, nx=45, ny=19)
+    for prec, batch in ((harm.HARM_PREC_MIXED, 256), (harm.HARM_PREC_FP64, 0)):
+        sc = harm.harm_scene_create(d, prec)
+        info = harm.harm_scene_query(sc)
+        sc.close()
+        assert (info["n_facets"], info["n_pulses"], info["n_range"]) == (45 * 19, 300, d["n_range"])
+        assert (info["n_channels"], info["n_waves"]) == (len(d["rx"]), d["n_omega"] * d["n_theta"])
+        assert (info["precision"], info["pulse_batch"]) == (prec, batch)
+        assert abs(info["range_bin_m"] - 299792458.0 / d["fs_hz"]) < 1e-12
+        want = [oracle.range_start(d, c) for c in range(len(d["rx"]))]
+        assert np.allclose(info["range_start_m"], want, rtol=0, atol=1e-6)
+
+
 def test_empty_window_is_noop():
     import torch
     d = hs.small_static()
