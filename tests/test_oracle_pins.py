@@ -374,6 +374,72 @@ def test_point_target_kaiser_taps():
         assert abs(iq[k] - s * h) < 1e-7 * abs(s)
 
 
+def _mp_steered_axes(p, vel):
+    """Azimuth / elevation axes of an antenna at p steered to the scene centre
+    (mpmath, from the reading of the paper: boresight toward the origin, azimuth
+    = velocity with its boresight part removed, elevation = boresight x azimuth)."""
+    r = kin.norm(p)
+    b = [-x / r for x in p]
+    v = kin.vec(vel)
+    vb = kin.dot(v, b)
+    t = [v[i] - vb * b[i] for i in range(3)]
+    tn = kin.norm(t)
+    a = [x / tn for x in t]
+    e = [b[1] * a[2] - b[2] * a[1], b[2] * a[0] - b[0] * a[2], b[0] * a[1] - b[1] * a[0]]
+    return a, e
+
+
+def _mp_sinc2_gain(len_az, len_el, lam, d, a, e):
+    def sinc(x):
+        return mp.mpf(1) if x == 0 else mp.sin(mp.pi * x) / (mp.pi * x)
+    return (sinc(mp.mpf(len_az) * kin.dot(d, a) / lam) ** 2
+            * sinc(mp.mpf(len_el) * kin.dot(d, e) / lam) ** 2)
+
+
+@pytest.mark.parametrize("n", [0, 700, 2047])
+def test_off_centre_amplitude(n):
+    """|contribution| of a static facet far from the scene centre (Eq. 3, Eq. 16):
+    sqrt(sigma0 A) |z| G_t G_r Rbar_t Rbar_r / (r_t r_r), every factor evaluated
+    here at 50 digits from the descriptor alone: ranges to the facet and to the
+    scene centre from the light-time solution, sinc^2 field gains of both antennas
+    steered to the scene centre, and |z| = sqrt(-ln u1) from the Philox word (the
+    Box-Muller radius). At the patch corners the range ratio departs from 1 by
+    ~1e-3 and the transmit gain from 1 by ~0.3, so an inverted or missing range
+    factor, a gain applied as power instead of field weight, or the wrong antenna's
+    pattern fails by orders of magnitude more than the tolerance."""
+    d = hs.ati_scene(n_pulses=2048, nx=2000, ny=1000)
+    d.update(static_surface=1, n_omega=0, n_theta=0)
+    lam = kin.C / mp.mpf(d["f0_hz"])
+    nx, ny = d["nx"], d["ny"]
+    facets = [0, nx - 1, (ny - 1) * nx, ny * nx - 1, (ny // 2) * nx + 37]
+    epoch = n // d["epoch_pulses"]
+    seed = d["speckle_seed"]
+    for c in (0, 2, 3, 5):
+        g = kin.pulse(d, n, c)
+        at, et = _mp_steered_axes(g["ptx"], d["tx"]["vel"])
+        ar, er = _mp_steered_axes(g["prx"], d["rx"][c]["vel"])
+        for f in facets:
+            x, y = kin.facet_xy(d, f)
+            xf = [x, y, mp.mpf(0)]
+            vt, vr = kin.sub(xf, g["ptx"]), kin.sub(xf, g["prx"])
+            rt, rr = kin.norm(vt), kin.norm(vr)
+            gt = _mp_sinc2_gain(d["tx"]["len_az"], d["tx"]["len_el"], lam, [v / rt for v in vt], at, et)
+            gr = _mp_sinc2_gain(d["rx"][c]["len_az"], d["rx"][c]["len_el"], lam, [v / rr for v in vr], ar, er)
+            w0 = oracle.philox4x32_10([f, 0, epoch, 0], [seed & 0xFFFFFFFF, seed >> 32])[0]
+            zabs = mp.sqrt(-mp.log((mp.mpf(w0) + 1) / mp.mpf(2) ** 32))
+            want = (mp.sqrt(mp.mpf(d["sigma0_base"]) * mp.mpf(d["facet_m"]) ** 2) * zabs * gt * gr
+                    * g["rt"] * g["rr"] / (rt * rr))
+            val, p = oracle.contribution(d, n, c, f, [0.0, 0.0, 0.0])
+            assert abs(abs(val) / float(want) - 1.0) < 1e-11, (n, c, f, abs(val), float(want))
+            # the bin position of the same contribution
+            dr = kin.C / mp.mpf(d["fs_hz"])
+            assert abs(p - float((rt + rr - kin.range_start(d, c)) / dr)) < 1e-8
+            # the geometry really is off centre: the factors being pinned are not 1
+            if f != (ny // 2) * nx + 37:
+                assert abs(float(g["rt"] * g["rr"] / (rt * rr)) - 1.0) > 5e-4
+    assert float(gt) < 0.99 or float(gr) < 0.99
+
+
 def test_bistatic_doppler_phase_history():
     """Corner facet over the burst: the pulse-to-pulse phase equals -K0 times the
     exact bistatic range history, and its central difference matches the closed
