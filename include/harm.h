@@ -13,7 +13,10 @@
  *   - Frame: flat-earth local frame, x along-track, y ground range away from the
  *     radars, z up, origin at the scene centre on the mean surface [m].
  *   - Device memory passed in (iq, state, residual, gradients) belongs to the
- *     caller and must be device memory of the current CUDA device. The scene owns
+ *     caller and must be device memory of the current CUDA device whose allocation
+ *     extends over every byte the call touches (both are checked before any launch:
+ *     HARM_E_INVALID otherwise; a buffer carved from a larger allocation is only
+ *     checked against that allocation's end). The scene owns
  *     only its own tables (and, once harm_echo_accumulate_host has been called,
  *     that call's device ring and streams); no other call allocates.
  *   - Every call is asynchronous on the scene's CUDA stream. A returned status
@@ -231,8 +234,9 @@ typedef struct harm_batch harm_batch; /* opaque, owned by the library */
    copies their launch arguments (cells, u-v grids) when it is created, so a
    scene changed afterwards needs a new batch. All scenes share the surface model
    (cwm) and the pattern kind (with or without u-v grids). The work
-   list is every (scene, 32 x rows facet tile, 32-pulse batch) item over the full
-   burst of every scene, largest scenes first. Errors: HARM_E_INVALID (NULL,
+   list is every (scene, 32 x rows facet tile, pulse window) item over the full
+   burst of every scene, largest scenes first; a pulse window is the mixed path's
+   time-Taylor window (harm_scene_info.pulse_batch pulses). Errors: HARM_E_INVALID (NULL,
    n_scenes < 1, mixed devices, channel counts or tap settings),
    HARM_E_UNSUPPORTED (an FP64 scene), HARM_E_OOM, HARM_E_CUDA. */
 harm_status harm_batch_create(harm_scene *const *scenes, int32_t n_scenes, harm_batch **out);

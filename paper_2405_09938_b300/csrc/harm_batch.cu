@@ -133,25 +133,25 @@ harm::BatchLaunch launch_desc(harm_batch *b, int total)
     return L;
 }
 
+size_t iq_bytes(const harm_scene *s)
+{
+    return (size_t)s->desc.n_channels * s->desc.n_pulses * s->desc.n_range * 8;
+}
+
 harm_status set_outputs(harm_batch *b, void *const *iq)
 {
     if (!iq) return fail(HARM_E_INVALID, "iq_dev is NULL");
     const int n = (int)b->scenes.size();
     for (int s = 0; s < n; ++s) {
         if (!iq[s]) return fail(HARM_E_INVALID, "iq_dev[%d] is NULL", s);
-        cudaPointerAttributes a;
-        BCUDA(cudaPointerGetAttributes(&a, iq[s]), "cudaPointerGetAttributes");
-        if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
-            return fail(HARM_E_INVALID, "iq_dev[%d] is not device memory", s);
+        char what[32];
+        snprintf(what, sizeof(what), "iq_dev[%d]", s);
+        harm_status st = harm::check_device_span(iq[s], iq_bytes(b->scenes[s]), what);
+        if (st != HARM_OK) return st;
     }
     BCUDA(cudaMemcpyAsync(b->d_iq, iq, n * sizeof(void *), cudaMemcpyHostToDevice, b->stream), "upload outputs");
     BCUDA(cudaStreamSynchronize(b->stream), "upload outputs");
     return HARM_OK;
-}
-
-size_t iq_bytes(const harm_scene *s)
-{
-    return (size_t)s->desc.n_channels * s->desc.n_pulses * s->desc.n_range * 8;
 }
 
 void drop_graph(harm_batch *b)

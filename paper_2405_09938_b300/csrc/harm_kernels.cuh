@@ -70,6 +70,10 @@ struct WaveSets {
 };
 
 harm_status build_scene_tables(harm_scene *s);
+// Check that p is device memory of the current device and that the allocation
+// holding it extends at least `bytes` past p (HARM_E_INVALID with a message
+// otherwise; NULL is invalid).
+harm_status check_device_span(const void *p, size_t bytes, const char *what);
 void release_host_ring(harm_scene *s);  // copy stream, events and ring of harm_echo_accumulate_host
 harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps, const WaveSets &waves);
 // Separable phasor tables of every wave set, computed on the device in FP64 and

@@ -88,12 +88,9 @@ extern "C" harm_status harm_batch_run_noalloc(harm_scene *const *scenes, int32_t
             return fail(HARM_E_INVALID, "scenes must share taps and kaiser_beta");
         if (harm::batch_variant(sc) != harm::batch_variant(scenes[0]))
             return fail(HARM_E_INVALID, "scenes must share the surface model (CWM) and the pattern kind (u-v grids)");
-        cudaPointerAttributes a;
-        if (cudaPointerGetAttributes(&a, iq_dev[s]) != cudaSuccess ||
-            (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
-            cudaGetLastError();
-            return fail(HARM_E_INVALID, "an output pointer is not device memory");
-        }
+        const size_t bytes = (size_t)sc->desc.n_channels * sc->desc.n_pulses * sc->desc.n_range * 8;
+        harm_status st = harm::check_device_span(iq_dev[s], bytes, "an output buffer");
+        if (st != HARM_OK) return st;
     }
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != scenes[0]->device)

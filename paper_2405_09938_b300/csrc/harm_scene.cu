@@ -330,7 +330,37 @@ harm_status check_device(const harm_scene *s)
     return HARM_OK;
 }
 
-harm_status check_ptr(const void *p, const char *what)
+harm_status check_ptr(const void *p, size_t bytes, const char *what)
+{
+    return harm::check_device_span(p, bytes, what);
+}
+
+// Driver query of the allocation that holds a device address (base, size),
+// fetched through the runtime so that the library does not link the driver
+// library itself; null when the driver does not offer it.
+typedef int (*AddressRangeFn)(unsigned long long *base, size_t *size, unsigned long long ptr);
+
+AddressRangeFn address_range_fn()
+{
+    static AddressRangeFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<AddressRangeFn>(f);
+    }();
+    return fn;
+}
+
+}  // namespace
+
+namespace harm {
+
+harm_status check_device_span(const void *p, size_t bytes, const char *what)
 {
     if (!p) return fail(HARM_E_INVALID, "%s is NULL", what);
     cudaPointerAttributes a;
@@ -338,10 +368,28 @@ harm_status check_ptr(const void *p, const char *what)
     if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes");
     if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
         return fail(HARM_E_INVALID, "%s is not device memory", what);
+    int dev = -1;
+    HARM_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (a.type == cudaMemoryTypeDevice && a.device != dev)
+        return fail(HARM_E_INVALID, "%s is memory of device %d, the current device is %d", what, a.device, dev);
+    if (a.type == cudaMemoryTypeDevice && bytes > 0) {
+        if (AddressRangeFn fn = address_range_fn()) {
+            unsigned long long base = 0;
+            size_t size = 0;
+            const unsigned long long ptr = (unsigned long long)(uintptr_t)p;
+            if (fn(&base, &size, ptr) == 0 && ptr >= base) {
+                const size_t avail = (size_t)(base + size - ptr);
+                if (bytes > avail)
+                    return fail(HARM_E_INVALID,
+                                "%s: the call touches %zu bytes, its allocation holds %zu from the pointer", what,
+                                bytes, avail);
+            }
+        }
+    }
     return HARM_OK;
 }
 
-}  // namespace
+}  // namespace harm
 
 namespace harm {
 harm_status set_error(harm_status s, const char *msg)
@@ -426,11 +474,11 @@ harm_status harm_scene_set_cells(harm_scene *s, int32_t ncx, int32_t ncy, double
     if (ncx < 1 || ncy < 1 || !(cell_m > 0) || (int64_t)ncx * ncy > (1 << 27))
         return fail(HARM_E_INVALID, "bad cell grid %d x %d of %g m", ncx, ncy, cell_m);
     if (sigma0_dev) {
-        harm_status st = check_ptr(sigma0_dev, "sigma0_dev");
+        harm_status st = check_ptr(sigma0_dev, (size_t)ncx * ncy * sizeof(double), "sigma0_dev");
         if (st != HARM_OK) return st;
     }
     if (uv_dev) {
-        harm_status st = check_ptr(uv_dev, "uv_dev");
+        harm_status st = check_ptr(uv_dev, (size_t)ncx * ncy * 2 * sizeof(double), "uv_dev");
         if (st != HARM_OK) return st;
     }
     s->dev.ncx = ncx;
@@ -516,7 +564,9 @@ harm_status harm_facets_generate(harm_scene *s, int32_t n0, int32_t np, void *st
     if (st != HARM_OK) return st;
     if ((st = check_device(s)) != HARM_OK) return st;
     if (np == 0) return HARM_OK;
-    if ((st = check_ptr(state_dev, "state_dev")) != HARM_OK) return st;
+    const size_t state_bytes = (size_t)np * (s->desc.cwm ? 8 : 3) * (size_t)s->nf *
+                               (s->desc.precision == HARM_PREC_FP64 ? sizeof(double) : sizeof(float));
+    if ((st = check_ptr(state_dev, state_bytes, "state_dev")) != HARM_OK) return st;
     cudaError_t e = harm::launch_generate(s, n0, np, state_dev);
     if (e != cudaSuccess) return cuda_fail(e, "facet generator launch");
     return HARM_OK;
@@ -530,8 +580,8 @@ harm_status harm_echo_accumulate(harm_scene *s, int32_t n0, int32_t np, void *iq
     if ((st = check_device(s)) != HARM_OK) return st;
     if (dtype != HARM_C64 && dtype != HARM_C128) return fail(HARM_E_INVALID, "unknown dtype %d", (int)dtype);
     if (np == 0) return HARM_OK;
-    if ((st = check_ptr(iq_dev, "iq_dev")) != HARM_OK) return st;
     size_t bytes = (size_t)s->desc.n_channels * np * s->desc.n_range * (dtype == HARM_C64 ? 8 : 16);
+    if ((st = check_ptr(iq_dev, bytes, "iq_dev")) != HARM_OK) return st;
     if (zero_first) HARM_CUDA(cudaMemsetAsync(iq_dev, 0, bytes, s->stream), "cudaMemsetAsync iq");
     cudaError_t e = harm::launch_accumulate(s, n0, np, iq_dev, dtype);
     if (e != cudaSuccess) return cuda_fail(e, "echo accumulator launch");
@@ -547,9 +597,13 @@ harm_status harm_echo_adjoint(harm_scene *s, int32_t n0, int32_t np, const void 
     if (dtype != HARM_C64 && dtype != HARM_C128) return fail(HARM_E_INVALID, "unknown dtype %d", (int)dtype);
     if (s->dev.ncx == 0) return fail(HARM_E_INVALID, "adjoint needs per-cell fields (harm_scene_set_cells)");
     if (np == 0) return HARM_OK;
-    if ((st = check_ptr(resid_dev, "resid_dev")) != HARM_OK) return st;
-    if (grad_sigma0_dev && (st = check_ptr(grad_sigma0_dev, "grad_sigma0_dev")) != HARM_OK) return st;
-    if (grad_uv_dev && (st = check_ptr(grad_uv_dev, "grad_uv_dev")) != HARM_OK) return st;
+    const size_t rbytes = (size_t)s->desc.n_channels * np * s->desc.n_range * (dtype == HARM_C64 ? 8 : 16);
+    const size_t cells = (size_t)s->dev.ncx * s->dev.ncy;
+    if ((st = check_ptr(resid_dev, rbytes, "resid_dev")) != HARM_OK) return st;
+    if (grad_sigma0_dev && (st = check_ptr(grad_sigma0_dev, cells * sizeof(double), "grad_sigma0_dev")) != HARM_OK)
+        return st;
+    if (grad_uv_dev && (st = check_ptr(grad_uv_dev, cells * 2 * sizeof(double), "grad_uv_dev")) != HARM_OK)
+        return st;
     cudaError_t e = harm::launch_adjoint(s, n0, np, resid_dev, dtype, grad_sigma0_dev, grad_uv_dev);
     if (e == cudaErrorNotSupported) return fail(HARM_E_UNSUPPORTED, "adjoint not available for this scene");
     if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");

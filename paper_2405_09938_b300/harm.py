@@ -186,12 +186,14 @@ def _stream_handle(stream):
 class Scene:
     """Owning handle of a ``harm_scene``."""
 
-    def __init__(self, ptr, desc: dict, precision: int, stream):
+    def __init__(self, ptr, desc: dict, precision: int, stream, device: int = -1):
         self._ptr = ptr
         self.desc = desc
         self.precision = precision
         self.stream = stream
+        self.device = device
         self._cells = None
+        self._ncells = 0
 
     @property
     def handle(self):
@@ -226,7 +228,8 @@ def harm_scene_create(desc: dict, precision: int = HARM_PREC_FP64, stream=None) 
     out = C.c_void_p()
     _check(lib.harm_scene_create(C.byref(s), C.c_void_p(_stream_handle(stream)), C.byref(out)))
     del keep
-    scene = Scene(out, desc, precision, stream)
+    import torch
+    scene = Scene(out, desc, precision, stream, torch.cuda.current_device())
     # u-v gain grids listed in the descriptor dictionary ("tx" or channel index)
     for ant, pat in (desc.get("patterns") or {}).items():
         harm_scene_set_pattern(scene, -1 if ant == "tx" else int(ant), pat)
@@ -267,30 +270,59 @@ def harm_scene_query(scene: Scene) -> dict:
             "range_start_m": np.array(info.range_start_m[:info.n_channels])}
 
 
-def _dev_ptr(t, what):
+def _dev_ptr(t, what, size=None, dtype=None):
+    """Device address of a contiguous CUDA tensor. With `size` = (scene, numel),
+    also checks that the tensor holds exactly numel elements (of `dtype`, when
+    given) on the scene's device: the library reads or writes that many elements
+    from the address."""
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise HarmError(HARM_E_INVALID, "%s must be a CUDA tensor" % what)
     if not t.is_contiguous():
         raise HarmError(HARM_E_INVALID, "%s must be contiguous" % what)
+    if dtype is not None and t.dtype != dtype:
+        raise HarmError(HARM_E_INVALID, "%s must be %s, not %s" % (what, dtype, t.dtype))
+    if size is not None:
+        scene, numel = size
+        if t.numel() != numel:
+            raise HarmError(HARM_E_INVALID, "%s holds %d elements, the call needs %d" % (what, t.numel(), numel))
+        if scene.device >= 0 and t.device.index != scene.device:
+            raise HarmError(HARM_E_INVALID, "%s is on cuda:%s, the scene on cuda:%d"
+                            % (what, t.device.index, scene.device))
     return C.c_void_p(t.data_ptr())
+
+
+def _iq_numel(scene, np_):
+    return len(scene.desc["rx"]) * np_ * scene.desc["n_range"]
+
+
+def _n_facets(scene):
+    return scene.desc["nx"] * scene.desc["ny"]
 
 
 def harm_scene_set_cells(scene: Scene, ncx, ncy, cell_m, sigma0=None, uv=None):
     """Per-cell NRCS base (float64 CUDA tensor [ncy, ncx]) and current
     ([ncy, ncx, 2]) on cells of cell_m metres; either may be None. The tensors are
     kept alive with the scene."""
-    sp = _dev_ptr(sigma0, "sigma0") if sigma0 is not None else None
-    up = _dev_ptr(uv, "uv") if uv is not None else None
+    import torch
+    nce = int(ncx) * int(ncy)
+    sp = _dev_ptr(sigma0, "sigma0", (scene, nce), torch.float64) if sigma0 is not None else None
+    up = _dev_ptr(uv, "uv", (scene, 2 * nce), torch.float64) if uv is not None else None
     _check(load_library().harm_scene_set_cells(scene.handle, ncx, ncy, cell_m, sp, up))
     scene._cells = (sigma0, uv)
+    scene._ncells = nce
 
 
 def harm_facets_generate(scene: Scene, n0: int, np_: int, state):
     """Facet states of pulses [n0, n0 + np_) into `state`, a CUDA tensor
     [np_][F][n_facets] (float64 for FP64 scenes, float32 for mixed; F = 3, or 8
     with the Choppy Wave Model)."""
-    _check(load_library().harm_facets_generate(scene.handle, n0, np_, _dev_ptr(state, "state")))
+    import torch
+    nfield = 8 if scene.desc.get("cwm") else 3
+    dt = torch.float64 if scene.precision == HARM_PREC_FP64 else torch.float32
+    _dev_ptr(state, "state")
+    ptr = _dev_ptr(state, "state", (scene, np_ * nfield * _n_facets(scene)), dt)
+    _check(load_library().harm_facets_generate(scene.handle, n0, np_, ptr))
 
 
 def _dtype_code(t):
@@ -306,8 +338,10 @@ def harm_echo_accumulate(scene: Scene, n0: int, np_: int, iq, zero_first: bool =
     """Add the echo of pulses [n0, n0 + np_) into `iq`, a contiguous CUDA tensor
     [n_channels][np_][n_range] (complex64 or complex128), cleared first unless
     zero_first is False. Asynchronous on the scene's stream."""
-    _check(load_library().harm_echo_accumulate(scene.handle, n0, np_, _dev_ptr(iq, "iq"),
-                                               _dtype_code(iq), 1 if zero_first else 0))
+    _dev_ptr(iq, "iq")
+    ptr = _dev_ptr(iq, "iq", (scene, _iq_numel(scene, np_)))
+    _check(load_library().harm_echo_accumulate(scene.handle, n0, np_, ptr, _dtype_code(iq),
+                                               1 if zero_first else 0))
 
 
 def harm_echo_accumulate_host(scene: Scene, n0: int, np_: int, iq_host, block_pulses: int = 0):
@@ -319,6 +353,9 @@ def harm_echo_accumulate_host(scene: Scene, n0: int, np_: int, iq_host, block_pu
         raise HarmError(HARM_E_INVALID, "iq_host must be a CPU tensor")
     if not iq_host.is_contiguous():
         raise HarmError(HARM_E_INVALID, "iq_host must be contiguous")
+    if iq_host.numel() != _iq_numel(scene, np_):
+        raise HarmError(HARM_E_INVALID, "iq_host holds %d elements, the call needs %d"
+                        % (iq_host.numel(), _iq_numel(scene, np_)))
     _check(load_library().harm_echo_accumulate_host(scene.handle, n0, np_, C.c_void_p(iq_host.data_ptr()),
                                                     _dtype_code(iq_host), block_pulses))
 
@@ -327,10 +364,15 @@ def harm_echo_adjoint(scene: Scene, n0: int, np_: int, resid, grad_sigma0=None, 
     """Add the gradients of sum |IQ - target|^2 for the residual `resid` (IQ -
     target, same layout and dtype as the IQ) to grad_sigma0 [ncy, ncx] and grad_uv
     [ncy, ncx, 2] (float64 CUDA tensors, either may be None). Needs cells."""
-    gs = _dev_ptr(grad_sigma0, "grad_sigma0") if grad_sigma0 is not None else None
-    gu = _dev_ptr(grad_uv, "grad_uv") if grad_uv is not None else None
-    _check(load_library().harm_echo_adjoint(scene.handle, n0, np_, _dev_ptr(resid, "resid"),
-                                            _dtype_code(resid), gs, gu))
+    import torch
+    _dev_ptr(resid, "resid")
+    rp = _dev_ptr(resid, "resid", (scene, _iq_numel(scene, np_)))
+    nce = scene._ncells
+    if nce == 0 and (grad_sigma0 is not None or grad_uv is not None):
+        raise HarmError(HARM_E_INVALID, "the adjoint needs per-cell fields (harm_scene_set_cells)")
+    gs = _dev_ptr(grad_sigma0, "grad_sigma0", (scene, nce), torch.float64) if grad_sigma0 is not None else None
+    gu = _dev_ptr(grad_uv, "grad_uv", (scene, 2 * nce), torch.float64) if grad_uv is not None else None
+    _check(load_library().harm_echo_adjoint(scene.handle, n0, np_, rp, _dtype_code(resid), gs, gu))
 
 
 def harm_scene_sync(scene: Scene):
@@ -363,15 +405,17 @@ class Batch:
             pass
 
 
-def _ptr_array(tensors, what):
+def _ptr_array(tensors, what, scenes):
+    """Pointer array of one complex64 IQ tensor per scene, each checked to hold the
+    scene's whole burst [n_channels][n_pulses][n_range] on the scene's device."""
+    import torch
+    if len(tensors) != len(scenes):
+        raise HarmError(HARM_E_INVALID, "%d %s tensors for %d scenes" % (len(tensors), what, len(scenes)))
     arr = (C.c_void_p * len(tensors))()
-    for i, t in enumerate(tensors):
-        import torch
+    for i, (t, sc) in enumerate(zip(tensors, scenes)):
         if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex64:
             raise HarmError(HARM_E_INVALID, "%s[%d] must be a complex64 CUDA tensor" % (what, i))
-        if not t.is_contiguous():
-            raise HarmError(HARM_E_INVALID, "%s[%d] must be contiguous" % (what, i))
-        arr[i] = t.data_ptr()
+        arr[i] = _dev_ptr(t, "%s[%d]" % (what, i), (sc, _iq_numel(sc, sc.desc["n_pulses"]))).value
     return arr
 
 
@@ -387,7 +431,7 @@ def harm_batch_create(scenes) -> Batch:
 def harm_batch_tune(batch: Batch, iqs):
     """Time 8- and 16-row tiles per scene-size class and keep the faster;
     overwrites the complex64 CUDA tensors `iqs` (one per scene). Synchronous."""
-    _check(load_library().harm_batch_tune(batch.handle, _ptr_array(iqs, "iq")))
+    _check(load_library().harm_batch_tune(batch.handle, _ptr_array(iqs, "iq", batch.scenes)))
 
 
 def harm_batch_tile_rows(batch: Batch):
@@ -406,7 +450,8 @@ def harm_batch_set_tile_rows(batch: Batch, rows):
 def harm_batch_run(batch: Batch, iqs, zero_first: bool = True):
     """Echo of every scene over its burst into `iqs` (complex64 CUDA tensors, one
     per scene), replayed from a CUDA graph."""
-    _check(load_library().harm_batch_run(batch.handle, _ptr_array(iqs, "iq"), 1 if zero_first else 0))
+    outs = _ptr_array(iqs, "iq", batch.scenes)
+    _check(load_library().harm_batch_run(batch.handle, outs, 1 if zero_first else 0))
 
 
 def harm_batch_destroy(batch: Batch):
@@ -417,6 +462,7 @@ def harm_batch_destroy(batch: Batch):
 def harm_batch_run_noalloc(scenes, iqs, zero_first: bool = True):
     """Allocation-free batched run (see include/harm.h): scratch in a fixed device
     array, at most 64 scenes per call, calls must not overlap on the GPU."""
+    outs = _ptr_array(iqs, "iq", scenes)
     arr = (C.c_void_p * len(scenes))(*[s.handle.value for s in scenes])
-    _check(load_library().harm_batch_run_noalloc(arr, len(scenes), _ptr_array(iqs, "iq"),
+    _check(load_library().harm_batch_run_noalloc(arr, len(scenes), outs,
                                                  1 if zero_first else 0))

@@ -157,3 +157,70 @@ def test_binding_rejects_bad_host_and_device_arguments():
     with pytest.raises(harm.HarmError) as e:
         harm.harm_echo_accumulate(_NullScene(), 0, 1, torch.zeros(4, dtype=torch.complex64))  # a CPU tensor
     assert "CUDA" in str(e.value)
+
+
+class _FakeCuda(__import__("torch").Tensor):
+    """A CPU tensor that reports itself as a CUDA tensor on cuda:0, so that the
+    binding's size and device checks can run without a GPU (the library is never
+    called: every case below must be refused first)."""
+
+    @property
+    def is_cuda(self):
+        return True
+
+    @property
+    def device(self):
+        import torch
+        return torch.device("cuda", 0)
+
+
+def _fake(shape, dtype):
+    import torch
+    return torch.zeros(shape, dtype=dtype).as_subclass(_FakeCuda)
+
+
+def test_binding_refuses_wrong_sized_or_misplaced_buffers():
+    """Output and input tensors must hold exactly the elements the call touches,
+    on the scene's device, before anything reaches the library (an undersized
+    buffer would otherwise be written past its end on the device)."""
+    import torch
+
+    import harm_scenes as hs
+    harm.load_library(harm_build.build())
+    d = hs.ati_scene(n_pulses=16, nx=40, ny=20, n_range=256)
+
+    class _Scene:
+        desc = d
+        precision = harm.HARM_PREC_MIXED
+        device = 0
+        _ncells = 8
+
+        @property
+        def handle(self):
+            raise AssertionError("the library must not be called")
+
+    sc = _Scene()
+    nc, nr = len(d["rx"]), d["n_range"]
+    cases = [
+        lambda: harm.harm_echo_accumulate(sc, 0, 4, _fake((nc, 3, nr), torch.complex64)),
+        lambda: harm.harm_echo_accumulate(sc, 0, 4, _fake((nc, 4, nr + 1), torch.complex128)),
+        lambda: harm.harm_facets_generate(sc, 0, 2, _fake((2, 3, 20 * 40 - 1), torch.float32)),
+        lambda: harm.harm_facets_generate(sc, 0, 2, _fake((2, 3, 20 * 40), torch.float64)),
+        lambda: harm.harm_echo_adjoint(sc, 0, 4, _fake((nc, 4, nr - 1), torch.complex64)),
+        lambda: harm.harm_echo_adjoint(sc, 0, 4, _fake((nc, 4, nr), torch.complex64),
+                                       grad_sigma0=_fake((7,), torch.float64)),
+        lambda: harm.harm_echo_adjoint(sc, 0, 4, _fake((nc, 4, nr), torch.complex64),
+                                       grad_uv=_fake((8,), torch.float64)),
+        lambda: harm.harm_scene_set_cells(sc, 4, 2, 10.0, _fake((9,), torch.float64), None),
+        lambda: harm.harm_batch_run_noalloc([sc], [_fake((nc, 15, nr), torch.complex64)]),
+        lambda: harm.harm_batch_run_noalloc([sc, sc], [_fake((nc, 16, nr), torch.complex64)]),
+    ]
+    for i, case in enumerate(cases):
+        with pytest.raises(harm.HarmError) as e:
+            case()
+        assert e.value.status == harm.HARM_E_INVALID, i
+    # a buffer of the right size on another device
+    sc.device = 1
+    with pytest.raises(harm.HarmError) as e:
+        harm.harm_echo_accumulate(sc, 0, 4, _fake((nc, 4, nr), torch.complex64))
+    assert "cuda:1" in str(e.value)
