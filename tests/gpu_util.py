@@ -44,3 +44,32 @@ def ati_phase_bias(got, want, a, b):
     w = np.sum(want[a] * np.conj(want[b]))
     d = np.angle(g) - np.angle(w)
     return float((d + np.pi) % (2 * np.pi) - np.pi)
+
+
+def peak_err(got, want):
+    """Largest per-element error, each normalised by the peak magnitude of its
+    (channel, pulse) row of the reference: max_k |got - want| / max_k |want|.
+    Unlike the relative RMS, this does not let one facet's misplaced bin or tap
+    disappear in the sum over a large scene (rows without signal are skipped)."""
+    g = np.asarray(got).reshape(-1, np.asarray(got).shape[-1])
+    w = np.asarray(want).reshape(-1, np.asarray(want).shape[-1])
+    peak = np.abs(w).max(axis=1)
+    rows = peak > 0
+    if not rows.any():
+        return float(np.abs(g).max())
+    return float((np.abs(g - w).max(axis=1)[rows] / peak[rows]).max())
+
+
+# Per-element bound relative to the RMS bound: the largest error of a row is a few
+# times its RMS error, and a row's peak a few times its RMS value.
+ELEM_FACTOR = 10.0
+
+
+def assert_iq(got, want, tol, elem_tol=None):
+    """IQ relative RMS below tol and every element within elem_tol (default
+    ELEM_FACTOR x tol) of its row's peak; returns (rel_rms, peak_err)."""
+    err, pe = rel_rms(got, want), peak_err(got, want)
+    lim = ELEM_FACTOR * tol if elem_tol is None else elem_tol
+    assert err < tol, "IQ rel RMS %.3e >= %.1e" % (err, tol)
+    assert pe < lim, "per-element error %.3e of the row peak >= %.1e (rel RMS %.3e)" % (pe, lim, err)
+    return err, pe

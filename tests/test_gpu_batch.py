@@ -7,7 +7,7 @@ import pytest
 import harm_scenes as hs
 import oracle
 from paper_2405_09938_b300 import harm
-from tests.gpu_util import rel_rms
+from tests.gpu_util import assert_iq, rel_rms
 
 pytestmark = pytest.mark.gpu
 
@@ -56,12 +56,12 @@ def test_batch_matches_single_scene_and_oracle():
     torch.cuda.synchronize()
     for d, t in zip(descs, iqs):
         got = t.cpu().numpy()
-        assert rel_rms(got, _single(d)) < 1e-5
+        assert_iq(got, _single(d), 1e-5)
     for i in (1, 3):
         d = descs[i]
         pulses = [0, d["n_pulses"] // 2, d["n_pulses"] - 1]
         want = oracle.echo(d, pulses)
-        assert rel_rms(iqs[i].cpu().numpy()[:, pulses, :], want) < 1e-4
+        assert_iq(iqs[i].cpu().numpy()[:, pulses, :], want, 1e-4)
     b.close()
     for s in scenes:
         s.close()
@@ -83,22 +83,22 @@ def test_batch_tune_and_graph_replay():
     # single-scene accumulator
     print("tuned tile rows:", rows)
     for d, a in zip(descs, first):
-        assert rel_rms(a, _single(d)) < 1e-5
+        assert_iq(a, _single(d), 1e-5)
     harm.harm_batch_run(b, iqs)  # graph replay
     torch.cuda.synchronize()
     for a, t in zip(first, iqs):
-        assert rel_rms(t.cpu().numpy(), a) < 1e-5
+        assert_iq(t.cpu().numpy(), a, 1e-5)
     # new output buffers: the graph is captured again
     iqs2 = _batch_outputs(descs)
     harm.harm_batch_run(b, iqs2)
     torch.cuda.synchronize()
     for a, t in zip(first, iqs2):
-        assert rel_rms(t.cpu().numpy(), a) < 1e-5
+        assert_iq(t.cpu().numpy(), a, 1e-5)
     # accumulate without clearing: doubles
     harm.harm_batch_run(b, iqs2, zero_first=False)
     torch.cuda.synchronize()
     for a, t in zip(first, iqs2):
-        assert rel_rms(t.cpu().numpy(), 2 * a) < 1e-5
+        assert_iq(t.cpu().numpy(), 2 * a, 1e-5)
     b.close()
     for s in scenes:
         s.close()
@@ -119,15 +119,15 @@ def test_batch_eight_row_tiles():
     harm.harm_batch_run(b, iqs)
     torch.cuda.synchronize()
     for d, t in zip(descs, iqs):
-        assert rel_rms(t.cpu().numpy(), _single(d)) < 1e-5
+        assert_iq(t.cpu().numpy(), _single(d), 1e-5)
     d = descs[3]
     pulses = [0, d["n_pulses"] - 1]
-    assert rel_rms(iqs[3].cpu().numpy()[:, pulses, :], oracle.echo(d, pulses)) < 1e-4
+    assert_iq(iqs[3].cpu().numpy()[:, pulses, :], oracle.echo(d, pulses), 1e-4)
     harm.harm_batch_set_tile_rows(b, [16, 8, 16, 8, 16])  # mixed heights, graph captured again
     harm.harm_batch_run(b, iqs)
     torch.cuda.synchronize()
     for d, t in zip(descs, iqs):
-        assert rel_rms(t.cpu().numpy(), _single(d)) < 1e-5
+        assert_iq(t.cpu().numpy(), _single(d), 1e-5)
     b.close()
     for s in scenes:
         s.close()

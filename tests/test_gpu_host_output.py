@@ -11,7 +11,7 @@ import pytest
 import harm_scenes as hs
 import oracle
 from paper_2405_09938_b300 import harm
-from tests.gpu_util import rel_rms, run_echo
+from tests.gpu_util import assert_iq, rel_rms, run_echo
 
 pytestmark = pytest.mark.gpu
 
@@ -48,11 +48,10 @@ def test_host_output_matches_device_output_ragged_blocks(block):
     want = run_echo(d, harm.HARM_PREC_MIXED, n0, np_, dtype="c64", scene=sc)
     sc.close()
     assert np.isfinite(got).all()
-    err = rel_rms(got, want)
-    print("block %d: host vs device output rel RMS %.2e" % (block, err))
-    assert err < TOL_SAME_KERNEL
+    err, pe = assert_iq(got, want, TOL_SAME_KERNEL)
+    print("block %d: host vs device output rel RMS %.2e, per-element %.2e" % (block, err, pe))
     for c in range(len(d["rx"])):
-        assert rel_rms(got[c], want[c]) < TOL_SAME_KERNEL
+        assert_iq(got[c], want[c], TOL_SAME_KERNEL)
 
 
 def test_host_output_complex128_against_oracle():
@@ -64,9 +63,8 @@ def test_host_output_complex128_against_oracle():
     sc.close()
     pulses = [0, 127, 128, 255, 256, 299]  # inside and at the edge of the default 256-pulse block, and the tail
     want = oracle.echo(d, pulses)
-    err = rel_rms(got[:, pulses, :], want)
-    print("host output (complex128) vs oracle: rel RMS %.2e" % err)
-    assert err < TOL_MIXED
+    err, pe = assert_iq(got[:, pulses, :], want, TOL_MIXED)
+    print("host output (complex128) vs oracle: rel RMS %.2e, per-element %.2e" % (err, pe))
 
 
 def test_host_output_ring_grows_and_is_reused():
@@ -77,8 +75,8 @@ def test_host_output_ring_grows_and_is_reused():
     b = _host_echo(sc, d, 0, 300, torch.complex64, 200)    # grows it
     c = _host_echo(sc, d, 10, 40, torch.complex64, 16)     # reuses the large ring
     sc.close()
-    assert rel_rms(a, c) < TOL_SAME_KERNEL
-    assert rel_rms(b[:, 10:50, :], a) < TOL_SAME_KERNEL
+    assert_iq(a, c, TOL_SAME_KERNEL)
+    assert_iq(b[:, 10:50, :], a, TOL_SAME_KERNEL)
 
 
 def test_host_output_rejects_pageable_memory():
@@ -105,7 +103,7 @@ def test_host_output_fp64_scene():
     got = _host_echo(sc, d, 0, 64, torch.complex128, 24)
     sc.close()
     want = oracle.echo(d, list(range(64)))
-    assert rel_rms(got, want) < 1e-7
+    assert_iq(got, want, 1e-7)
 
 
 def test_host_output_window_checks():

@@ -12,7 +12,7 @@ import pytest
 import harm_scenes as hs
 import oracle
 from paper_2405_09938_b300 import harm
-from tests.gpu_util import ati_phase_bias, rel_rms, run_echo, run_states
+from tests.gpu_util import assert_iq, ati_phase_bias, rel_rms, run_echo, run_states
 
 pytestmark = pytest.mark.gpu
 
@@ -57,7 +57,7 @@ def test_static_patch_fp64(taps):
     d["taps"] = taps
     got = run_echo(d, harm.HARM_PREC_FP64, 0, 64, "c128")
     want = oracle.echo(d, list(range(64)))
-    assert rel_rms(got, want) < TOL_FP64
+    assert_iq(got, want, TOL_FP64)
 
 
 def test_wave_scene_fp64_all_channels():
@@ -65,16 +65,16 @@ def test_wave_scene_fp64_all_channels():
     got = run_echo(d, harm.HARM_PREC_FP64, 0, 64, "c128")
     want = oracle.echo(d, list(range(64)))
     assert got.shape == want.shape == (6, 64, 1024)
-    assert rel_rms(got, want) < TOL_FP64
+    assert_iq(got, want, TOL_FP64)
     for c in range(6):
-        assert rel_rms(got[c], want[c]) < TOL_FP64
+        assert_iq(got[c], want[c], TOL_FP64)
 
 
 def test_fp64_path_c64_output():
     d = hs.small_static()
     got = run_echo(d, harm.HARM_PREC_FP64, 0, 64, "c64")
     want = oracle.echo(d, list(range(64)))
-    assert rel_rms(got, want) < 1e-6
+    assert_iq(got, want, 1e-6)
 
 
 # ------------------------------------------------------------------ mixed path
@@ -84,15 +84,14 @@ def test_static_patch_mixed(taps):
     d["taps"] = taps
     got = run_echo(d, harm.HARM_PREC_MIXED, 0, 64, "c64")
     want = oracle.echo(d, list(range(64)))
-    assert rel_rms(got, want) < TOL_MIXED
+    assert_iq(got, want, TOL_MIXED)
 
 
 def test_wave_scene_mixed_errors():
     d = small_wave_scene()
     got = run_echo(d, harm.HARM_PREC_MIXED, 0, 64, "c64")
     want = oracle.echo(d, list(range(64)))
-    err = rel_rms(got, want)
-    assert err < TOL_MIXED, err
+    assert_iq(got, want, TOL_MIXED)
     for sat in (0, 3):
         for a, b in ((0, 1), (1, 2), (0, 2)):
             assert abs(ati_phase_bias(got, want, sat + a, sat + b)) < 1e-4
@@ -102,7 +101,7 @@ def test_mixed_c128_output():
     d = small_wave_scene(n_pulses=40)
     got = run_echo(d, harm.HARM_PREC_MIXED, 0, 40, "c128")
     want = oracle.echo(d, list(range(40)))
-    assert rel_rms(got, want) < TOL_MIXED
+    assert_iq(got, want, TOL_MIXED)
 
 
 # ------------------------------------------------------------------ edges
@@ -114,7 +113,7 @@ def test_ragged_grid_and_unaligned_pulse_window():
     want = oracle.echo(d, list(range(n0, n0 + np_)))
     for prec, tol, dt in ((harm.HARM_PREC_FP64, TOL_FP64, "c128"), (harm.HARM_PREC_MIXED, TOL_MIXED, "c64")):
         got = run_echo(d, prec, n0, np_, dt)
-        assert rel_rms(got, want) < tol
+        assert_iq(got, want, tol)
 
 
 def test_sixteen_channels_maximum():
@@ -128,9 +127,9 @@ def test_sixteen_channels_maximum():
     want = oracle.echo(d, pulses)
     for prec, tol, dt in ((harm.HARM_PREC_FP64, TOL_FP64, "c128"), (harm.HARM_PREC_MIXED, TOL_MIXED, "c64")):
         got = run_echo(d, prec, 0, 40, dt)[:, pulses, :]
-        assert rel_rms(got, want) < tol
+        assert_iq(got, want, tol)
         for c in range(16):
-            assert rel_rms(got[c], want[c]) < tol
+            assert_iq(got[c], want[c], tol)
 
 
 def test_six_channels_without_shared_antennas():
@@ -143,9 +142,9 @@ def test_six_channels_without_shared_antennas():
     pulses = [0, 17, 39]
     want = oracle.echo(d, pulses)
     got = run_echo(d, harm.HARM_PREC_MIXED, 0, 40, "c64")[:, pulses, :]
-    assert rel_rms(got, want) < TOL_MIXED
+    assert_iq(got, want, TOL_MIXED)
     for c in range(6):
-        assert rel_rms(got[c], want[c]) < TOL_MIXED
+        assert_iq(got[c], want[c], TOL_MIXED)
 
 
 def test_echo_partly_outside_range_window():
@@ -160,7 +159,7 @@ def test_echo_partly_outside_range_window():
     assert np.abs(want[:, :, 0]).max() > 0 and np.abs(want[:, :, -1]).max() > 0
     for prec, tol, dt in ((harm.HARM_PREC_FP64, TOL_FP64, "c128"), (harm.HARM_PREC_MIXED, TOL_MIXED, "c64")):
         got = run_echo(cut, prec, 0, 16, dt)
-        assert rel_rms(got, want) < tol
+        assert_iq(got, want, tol)
 
 
 def test_single_facet_and_single_pulse():
@@ -169,7 +168,7 @@ def test_single_facet_and_single_pulse():
     want = oracle.echo(d, [2])
     for prec, tol, dt in ((harm.HARM_PREC_FP64, TOL_FP64, "c128"), (harm.HARM_PREC_MIXED, TOL_MIXED, "c64")):
         got = run_echo(d, prec, 2, 1, dt)
-        assert rel_rms(got, want) < tol
+        assert_iq(got, want, tol)
 
 
 def test_scene_query_reports_the_scene():
@@ -206,7 +205,7 @@ def test_accumulate_without_zeroing_adds():
     harm.harm_echo_accumulate(scene, 0, 8, iq, zero_first=False)
     harm.harm_scene_sync(scene)
     want = oracle.echo(d, list(range(8)))
-    assert rel_rms(iq.cpu().numpy(), 2 * want) < TOL_FP64
+    assert_iq(iq.cpu().numpy(), 2 * want, TOL_FP64)
     scene.close()
 
 
@@ -230,4 +229,4 @@ def test_repeat_runs_agree():
     d = small_wave_scene(n_pulses=32)
     a = run_echo(d, harm.HARM_PREC_MIXED, 0, 32, "c64")
     b = run_echo(d, harm.HARM_PREC_MIXED, 0, 32, "c64")
-    assert rel_rms(a, b) < 1e-6
+    assert_iq(a, b, 1e-6)

@@ -15,7 +15,7 @@ import pytest
 import harm_scenes as hs
 import oracle
 from paper_2405_09938_b300 import harm
-from tests.gpu_util import rel_rms, run_echo
+from tests.gpu_util import assert_iq, rel_rms, run_echo
 
 pytestmark = pytest.mark.gpu
 
@@ -47,9 +47,9 @@ VARIANTS = {
 def _check(d, prec, tol):
     got = run_echo(d, prec, 0, d["n_pulses"], "c128")[:, PULSES, :]
     want = oracle.echo(d, PULSES)
-    assert rel_rms(got, want) < tol, rel_rms(got, want)
+    assert_iq(got, want, tol)
     for c in range(len(d["rx"])):
-        assert rel_rms(got[c], want[c]) < tol
+        assert_iq(got[c], want[c], tol)
 
 
 @pytest.mark.parametrize("name", list(VARIANTS))
@@ -73,7 +73,7 @@ def test_variant_fp64_matches_oracle(name):
     got = run_echo(d, harm.HARM_PREC_FP64, 0, 48, "c128")
     pulses = [0, 17, 47]
     want = oracle.echo(d, pulses)
-    assert rel_rms(got[:, pulses, :], want) < TOL_FP64
+    assert_iq(got[:, pulses, :], want, TOL_FP64)
 
 
 def test_variant_changes_the_echo():
@@ -93,7 +93,7 @@ def test_ar1_truncated_restart_mid_burst():
     got = run_echo(d, harm.HARM_PREC_MIXED, n0, np_, "c128")
     pulses = [1024, 1060, 1099]
     want = oracle.echo(d, pulses)
-    assert rel_rms(got[:, [p - n0 for p in pulses], :], want) < TOL_MIXED
+    assert_iq(got[:, [p - n0 for p in pulses], :], want, TOL_MIXED)
 
 
 def test_cwm_generator_fields():
@@ -129,8 +129,8 @@ def test_uv_grid_set_and_removed():
     harm.harm_scene_sync(scene)
     without = iq.cpu().numpy()
     scene.close()
-    assert rel_rms(with_grid[:, [17], :], oracle.echo(dl, [17])) < TOL_MIXED
-    assert rel_rms(without[:, [17], :], oracle.echo(d, [17])) < TOL_MIXED
+    assert_iq(with_grid[:, [17], :], oracle.echo(dl, [17]), TOL_MIXED)
+    assert_iq(without[:, [17], :], oracle.echo(d, [17]), TOL_MIXED)
     # channel 6 does not exist; a grid with one node per axis is rejected
     other = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
     with pytest.raises(harm.HarmError):
@@ -182,7 +182,7 @@ def test_batch_of_variant_scenes():
     torch.cuda.synchronize()
     for d, t in zip(descs, iqs):
         pulses = [0, d["n_pulses"] - 1]
-        assert rel_rms(t.cpu().numpy()[:, pulses, :], oracle.echo(d, pulses)) < TOL_MIXED
+        assert_iq(t.cpu().numpy()[:, pulses, :], oracle.echo(d, pulses), TOL_MIXED)
     b.close()
     # scenes of different surface models do not batch together
     plain = harm.harm_scene_create(hs.ati_scene(n_pulses=50, nx=40, ny=33, n_range=1024), harm.HARM_PREC_MIXED)

@@ -7,7 +7,7 @@ import pytest
 
 import harm_scenes as hs
 from paper_2405_09938_b300 import harm
-from tests.gpu_util import rel_rms
+from tests.gpu_util import assert_iq, rel_rms
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +41,7 @@ def test_noalloc_matches_batch_run_twice():
         harm.harm_batch_run_noalloc(scenes, out, zero_first=True)
         torch.cuda.synchronize()
         for w, t in zip(want, out):
-            assert rel_rms(t.cpu().numpy(), w) < TOL
+            assert_iq(t.cpu().numpy(), w, TOL)
     for s in scenes:
         s.close()
 
