@@ -135,6 +135,52 @@ def test_adjoint_matches_fd_on_16_cells():
             assert abs(fd - guv_g[cy, cx, comp]) <= TOL_GRAD * gmax
 
 
+def test_adjoint_sigma0_matches_fd_on_8_cells():
+    """dL/dsigma0 of the GPU adjoint against central differences of the oracle's
+    FP64 misfit (the IQ goes as sqrt(sigma0), so the misfit is not linear in it;
+    step 1e-7 on sigma0 ~ 0.02, truncation ~1e-10 relative)."""
+    d = _scene(n_pulses=24, nx=64, ny=48, cell_m=16.0)
+    pulses = list(range(24))
+    tgt = oracle.echo(_perturbed(d), pulses)
+    r = oracle.echo(d, pulses) - tgt
+    gs_g, _ = _gpu_adjoint(d, 0, 24, r)
+    h = 1e-7
+    ncy, ncx = d["cells"]["ncy"], d["cells"]["ncx"]
+    gmax = np.abs(gs_g).max()
+    for q in np.linspace(0, ncx * ncy - 1, 8).astype(int):
+        cy, cx = q // ncx, q % ncx
+        up = d["cells"]["sigma0"].copy()
+        dn = d["cells"]["sigma0"].copy()
+        up[cy, cx] += h
+        dn[cy, cx] -= h
+        lp, _ = oracle.misfit(dict(d, cells=dict(d["cells"], sigma0=up)), pulses, tgt)
+        lm, _ = oracle.misfit(dict(d, cells=dict(d["cells"], sigma0=dn)), pulses, tgt)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gs_g[cy, cx]) <= TOL_GRAD * gmax, (cy, cx, fd, gs_g[cy, cx])
+
+
+def test_autograd_complex128_gradient_kept():
+    """A complex128 IQ (iq_dtype) and its complex128 incoming gradient go through
+    the adjoint without a cast to complex64."""
+    import torch
+    from paper_2405_09938_b300 import autograd as hag
+    d = _scene(n_pulses=16, nx=64, ny=40)
+    c = d["cells"]
+    scene = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
+    s0 = torch.tensor(c["sigma0"], dtype=torch.float64, device="cuda", requires_grad=True)
+    uv = torch.tensor(c["uv"], dtype=torch.float64, device="cuda", requires_grad=True)
+    tgt = torch.tensor(oracle.echo(_perturbed(d), list(range(16))), dtype=torch.complex128, device="cuda")
+    iq = hag.echo(s0, uv, scene, 0, 16, c["cell_m"], iq_dtype=torch.complex128)
+    assert iq.dtype == torch.complex128
+    loss = torch.sum(torch.abs(iq - tgt) ** 2)
+    loss.backward()
+    r = (iq.detach() - tgt).cpu().numpy()
+    gs_o, guv_o = oracle.adjoint(d, list(range(16)), r)
+    assert np.abs(s0.grad.cpu().numpy() - gs_o).max() <= TOL_GRAD * np.abs(gs_o).max()
+    assert np.abs(uv.grad.cpu().numpy() - guv_o).max() <= TOL_GRAD * np.abs(guv_o).max()
+    scene.close()
+
+
 def test_autograd_function_gradients():
     import torch
     from paper_2405_09938_b300 import autograd as hag
