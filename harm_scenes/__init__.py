@@ -11,11 +11,14 @@ centres move linearly, P(t) = pos0 + vel * t, with t = 0 at the first pulse.
 
 Workloads follow the instrument of the paper's Sec. II-B / Fig. 1 (Sentinel-1
 transmitter, two Harmony receivers about 250 km ahead and behind, three along-track
-phase centres each) and the raw-data generator of Sec. IV; sizes are the synthetic
-scenes described in the design notes: a 200 m static patch (the small case), a
-4 km x 2 km wave-covered ATI scene with 6 channels (the headline case), a
-20 km x 5 km mixed-precision scene, a 2 km x 1 km differentiable scene, and a batch
-of 48 uneven scenes.
+phase centres each) and the raw-data generator of Sec. IV, on 2 m facets: a 200 m
+static patch (100 x 100 facets, 64 pulses, 1 channel, 512 range samples; the small
+case), a 4 km x 2 km wave-covered ATI scene (2000 x 1000 facets, 2048 pulses,
+6 channels, 4096 range samples; the headline case), a 20 km x 5 km mixed-precision
+scene (10000 x 2500 facets, 4096 pulses, 3 channels), a 2 km x 1 km differentiable
+scene (1000 x 500 facets, 1024 pulses, 6 channels, 100 m cells), and a batch of 48
+uneven scenes (0.5 x 0.5 km to 8 x 4 km, 256 to 2048 pulses, 1024 to 8192 range
+samples).
 """
 from __future__ import annotations
 
