@@ -57,8 +57,13 @@ typedef enum {
 
 typedef enum {
     HARM_PREC_FP64 = 0,  /* every step in double precision */
-    HARM_PREC_MIXED = 1  /* FP64 only for per-pulse state, reference ranges and
+    HARM_PREC_MIXED = 1, /* FP64 only for per-pulse state, reference ranges and
                             per-tile range offsets; FP32 for the rest */
+    HARM_PREC_FP32 = 2   /* the plain method of HARM_PREC_FP64 with every per-facet
+                            step in single precision (per-pulse state built in FP64
+                            on the host and rounded): ranges, phases and taps carry
+                            FP32 rounding of the ~1e6 m ranges and ~1e5 rad phases,
+                            which is what the mixed path's FP64 references avoid */
 } harm_precision;
 
 /* One antenna phase centre moving linearly: P(t) = pos0 + vel * t, t = 0 at the
@@ -178,7 +183,7 @@ harm_status harm_scene_set_pattern(harm_scene *scene, int32_t antenna, int32_t n
 /* Facet generator (Sec. III surface; the per-tile surface synthesis of Sec. IV-B): writes
    the state of every facet for pulses [n0, n0 + np) at the bounce time of each
    pulse, to state_dev laid out [np][F][n_facets], in double for HARM_PREC_FP64
-   scenes and in float for HARM_PREC_MIXED scenes. F = 3 fields (eta, eta_x,
+   scenes and in float for HARM_PREC_MIXED and HARM_PREC_FP32 scenes. F = 3 fields (eta, eta_x,
    eta_y) for the linear surface; F = 8 with the Choppy Wave Model: (eta, eta_x,
    eta_y, D_x, D_y, dD_x/dx, dD_x/dy, dD_y/dy), D the horizontal displacement and
    every derivative taken with respect to the rest position.
@@ -292,6 +297,27 @@ harm_status harm_batch_destroy(harm_batch *batch);
    HARM_E_CUDA. */
 harm_status harm_batch_run_noalloc(harm_scene *const *scenes, int32_t n_scenes, void *const *iq_dev,
                                    int32_t zero_first);
+
+/* Index probe (diagnostic; the parity tests use it to compare the accumulator's
+   integer work bit for bit): runs the work items of harm_echo_accumulate over
+   pulses [n0, n0 + np) with the same per-facet code -- tile references, surface,
+   speckle, ranges -- up to the scatter, and instead of adding contributions
+   records, per facet f (grid index iy * nx + ix) and pulse j = n - n0:
+     bins_dev    [np][n_channels][n_facets] int32: first range bin of the facet's
+                 taps in each channel (floor(p) - 3 for the 8-tap kernel, floor(p)
+                 for the Eq. 17 box, p the bin position of Eq. 17's range sum);
+     speckle_dev [np][n_facets] complex (complex128 for HARM_PREC_FP64 scenes,
+                 complex64 otherwise): the speckle draw z of pulse n's coherence
+                 epoch (Eq. 7 at f_s = 0, or the recurrence of Eq. 10);
+     words_dev   [np][n_facets][4] uint32: the Philox4x32-10 words of counter
+                 (f, 0, epoch, 0) under the speckle key, the draw's source;
+     cells_dev   [n_facets] int32: the facet's cell index (-1 without cells).
+   All four are device buffers of the current device (none may be NULL); they
+   are overwritten. Every precision (the plain paths run their own accumulator
+   with the same recording). Asynchronous on the scene's stream.
+   Errors: HARM_E_INVALID (window, pointers), HARM_E_CUDA. */
+harm_status harm_probe_indices(harm_scene *scene, int32_t n0, int32_t np, int32_t *bins_dev, void *speckle_dev,
+                               uint32_t *words_dev, int32_t *cells_dev);
 
 /* Wait for the scene's stream and report device-side errors (bounded waits that
    timed out, bounds flags) raised since the last check. */

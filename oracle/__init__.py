@@ -134,6 +134,12 @@ def lib():
         L.or_num_threads.restype = C.c_int
         L.or_set_num_threads.argtypes = [C.c_int]
         L.or_set_num_threads.restype = None
+        L.or_bin_positions.argtypes = [C.POINTER(OrScene), C.c_int, C.POINTER(C.c_int), dp,
+                                       C.POINTER(C.c_int)]
+        L.or_bin_positions.restype = C.c_int
+        u32p = C.POINTER(C.c_uint32)
+        L.or_speckle_words.argtypes = [C.c_uint64, C.c_int64, u32p, u32p, u32p]
+        L.or_speckle_words.restype = None
         L.or_adjoint.argtypes = [C.POINTER(OrScene), C.c_int, C.POINTER(C.c_int), dp, dp, dp]
         L.or_adjoint.restype = C.c_int
         _lib = L
@@ -379,6 +385,32 @@ def echo(desc, pulses, facets=None):
         fp, nfac = fa.ctypes.data_as(C.POINTER(C.c_int64)), len(fa)
     lib().or_echo(sc.ref, len(pl), pl.ctypes.data_as(C.POINTER(C.c_int)), nfac, fp, _dptr(out))
     return out[..., 0] + 1j * out[..., 1]
+
+
+def bin_positions(desc, pulses):
+    """Fractional range-bin position p of every facet's contribution at the listed
+    pulses, p[i, c, iy, ix], and the facets' cell indices cells[iy, ix] (-1
+    without per-cell fields)."""
+    sc = Scene(desc)
+    pl = np.ascontiguousarray(pulses, dtype=np.int32)
+    nc, nx, ny = len(desc["rx"]), desc["nx"], desc["ny"]
+    p = np.zeros((len(pl), nc, ny, nx))
+    cells = np.zeros((ny, nx), dtype=np.int32)
+    lib().or_bin_positions(sc.ref, len(pl), pl.ctypes.data_as(C.POINTER(C.c_int)), _dptr(p),
+                           cells.ctypes.data_as(C.POINTER(C.c_int)))
+    return p, cells
+
+
+def speckle_words(seed, facets, epochs):
+    """Philox4x32-10 words of the speckle draws of (facet, epoch) pairs:
+    uint32 [n, 4]."""
+    f = np.ascontiguousarray(facets, dtype=np.uint32)
+    e = np.ascontiguousarray(np.broadcast_to(epochs, f.shape), dtype=np.uint32)
+    out = np.zeros((f.size, 4), dtype=np.uint32)
+    u32p = C.POINTER(C.c_uint32)
+    lib().or_speckle_words(int(seed), f.size, f.ctypes.data_as(u32p), e.ctypes.data_as(u32p),
+                           out.ctypes.data_as(u32p))
+    return out
 
 
 def num_threads():

@@ -799,6 +799,53 @@ int or_echo(const or_scene *s, int n_list, const int *pulses, int64_t n_fac, con
     return 0;
 }
 
+/* Bin positions of every facet at the listed pulses (for the parity of the
+   accumulator's integer bins): p_out[i][c][f] is the fractional range-bin
+   position p = (r_t + r_r - R0_c) / dr of facet f's contribution to channel c at
+   pulse pulses[i] (the p that `spread` turns into taps k = floor(p) - 3 ...
+   floor(p) + 4), and cell_out[f] its cell index (-1 without per-cell fields). */
+int or_bin_positions(const or_scene *s, int n_list, const int *pulses, double *p_out, int *cell_out)
+{
+    int nc = s->n_channels;
+    int64_t nf = (int64_t)s->nx * s->ny;
+    or_waves W;
+    waves_build(s, &W);
+    double *st = malloc(sizeof(double) * 8 * (nf > 0 ? nf : 1));
+    double r0[OR_MAXC];
+    for (int c = 0; c < nc; ++c) r0[c] = or_range_start(s, c);
+    for (int i = 0; i < n_list; ++i) {
+        int n = pulses[i];
+        facet_states_w(s, &W, n, st);
+        for (int c = 0; c < nc; ++c) {
+            or_pulse g;
+            or_pulse_state(s, n, c, &g);
+            double *row = p_out + ((int64_t)i * nc + c) * nf;
+#pragma omp parallel for schedule(static)
+            for (int64_t f = 0; f < nf; ++f) {
+                double state[8];
+                for (int k = 0; k < 8; ++k) state[k] = st[k * nf + f];
+                double sre, sim, p;
+                int cell;
+                contribution_full(s, &g, n, c, f, state, r0[c], &sre, &sim, &p, NULL, NULL, &cell);
+                row[f] = p;
+                if (i == 0 && c == 0 && cell_out) cell_out[f] = cell;
+            }
+        }
+    }
+    free(st);
+    waves_free(&W);
+    return 0;
+}
+
+/* Philox words of the speckle draws of count (facet, epoch) pairs:
+   out[4 q .. 4 q + 3] for counter (facet[q], 0, epoch[q], 0) under the speckle
+   key (the words or_speckle turns into a draw). */
+void or_speckle_words(uint64_t seed, int64_t count, const uint32_t *facet, const uint32_t *epoch, uint32_t *out)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < count; ++q) philox_draw(seed, facet[q], epoch[q], OR_STREAM_SPECKLE, out + 4 * q);
+}
+
 /* One facet's contribution (complex value and bin position) for tests:
    out = {re, im, p}. */
 void or_contribution(const or_scene *s, int n, int c, int64_t f, const double state[8], double *out)

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libharm.so")
-SOURCES = ["harm_scene.cu", "harm_dispatch.cu", "harm_batch.cu", "harm_noalloc.cu", "harm_host.cu", "echo_fp64.cu",
+SOURCES = ["harm_scene.cu", "harm_dispatch.cu", "harm_batch.cu", "harm_noalloc.cu", "harm_host.cu", "echo_plain.cu",
            "echo_mixed.cu",
            "echo_mixed_cwm.cu", "echo_mixed_lut.cu", "echo_mixed_cwm_lut.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

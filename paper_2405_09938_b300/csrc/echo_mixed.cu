@@ -17,6 +17,9 @@ cudaError_t mixed_adjoint_v2(const DevScene &, const MixedTables &, cudaStream_t
                              double *, double *);
 cudaError_t mixed_adjoint_v3(const DevScene &, const MixedTables &, cudaStream_t, int, int, const void *, harm_dtype,
                              double *, double *);
+cudaError_t mixed_probe_v1(const DevScene &, const MixedTables &, cudaStream_t, int, int, int *, void *, void *, int *);
+cudaError_t mixed_probe_v2(const DevScene &, const MixedTables &, cudaStream_t, int, int, int *, void *, void *, int *);
+cudaError_t mixed_probe_v3(const DevScene &, const MixedTables &, cudaStream_t, int, int, int *, void *, void *, int *);
 cudaError_t mixed_batch_v1(const BatchLaunch &, cudaStream_t);
 cudaError_t mixed_batch_v2(const BatchLaunch &, cudaStream_t);
 cudaError_t mixed_batch_v3(const BatchLaunch &, cudaStream_t);
@@ -55,6 +58,17 @@ cudaError_t launch_adjoint_mixed(const DevScene &S, const MixedTables &M, cudaSt
     case 2: return mixed_adjoint_v2(S, M, st, n0, np, resid, dtype, g_sigma, g_uv);
     case 3: return mixed_adjoint_v3(S, M, st, n0, np, resid, dtype, g_sigma, g_uv);
     default: return mixed_adjoint_v0(S, M, st, n0, np, resid, dtype, g_sigma, g_uv);
+    }
+}
+
+cudaError_t launch_probe_mixed(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, int *bins,
+                               void *speckle, void *words, int *cells)
+{
+    switch (mixed_variant(S)) {
+    case 1: return mixed_probe_v1(S, M, st, n0, np, bins, speckle, words, cells);
+    case 2: return mixed_probe_v2(S, M, st, n0, np, bins, speckle, words, cells);
+    case 3: return mixed_probe_v3(S, M, st, n0, np, bins, speckle, words, cells);
+    default: return mixed_probe_v0(S, M, st, n0, np, bins, speckle, words, cells);
     }
 }
 

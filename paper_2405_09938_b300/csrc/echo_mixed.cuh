@@ -849,6 +849,7 @@ struct FacetGeo {
 // Forward sink: warp pre-reduction into the CTA range tile of the channel.
 template <typename OutT>
 struct ScatterSink {
+    static constexpr bool kProbe = false;
     float *stage;
     float2 *tiles;    // [kTileBufs][nc][WT]
     OutT *iq;
@@ -882,6 +883,48 @@ struct ScatterSink {
         }
         warp_scatter<OutT>(stage, tile_c, tile_base, kba, va, ha, vre.x, vim.x, A.S.nr, grow, A.S.flags);
         warp_scatter<OutT>(stage, tile_c, tile_base, kbb, vb, hb, vre.y, vim.y, A.S.nr, grow, A.S.flags);
+    }
+};
+
+// Outputs of the index probe, indexed by facet grid position; pulses count
+// from the first pulse of the probed window.
+struct ProbeOut {
+    int *bins;        // [np][nc][ny][nx] first range bin of the facet's taps (k0 - 3; k0 for the box)
+    float2 *speckle;  // [np][ny][nx] speckle draw of the pulse's coherence epoch
+    uint4 *words;     // [np][ny][nx] Philox4x32-10 words that draw was made from
+    int *cells;       // [ny][nx] cell index of the facet (-1 without per-cell fields)
+};
+
+// Probe sink: the forward work item runs unchanged up to the scatter, and this
+// sink records the integer results the scatter would use (both facets' first
+// bins per channel) and the speckle of the pulse instead of adding anything.
+struct ProbeSink : ScatterSink<float> {
+    static constexpr bool kProbe = true;
+    ProbeOut out;
+    int ix, iya, iyb;  // the thread's facets (iyb < 0: one facet per thread)
+    int n, epoch;      // current pulse and its speckle epoch
+    float2 za, zb;     // the facets' speckle draws of that epoch
+    __device__ __forceinline__ void set_pulse(const MixedArgs &A, int n_, int buf)
+    {
+        ScatterSink<float>::set_pulse(A, n_, buf);
+        n = n_;
+    }
+    __device__ __forceinline__ void prepare(int, int, bool, bool) {}
+    __device__ __forceinline__ void one(const DevScene &S, int ch, int iy, int kb, float2 z)
+    {
+        const size_t plane = (size_t)S.nx * S.ny, at = (size_t)iy * S.nx + ix, p = (size_t)(n - n0);
+        out.bins[(p * S.nc + ch) * plane + at] = kb;
+        if (ch == 0) {
+            out.speckle[p * plane + at] = z;
+            const U32x4 w = philox_stream(S.speckle_seed, kStreamSpeckle, (uint32_t)at, (uint32_t)epoch);
+            out.words[p * plane + at] = make_uint4(w.x, w.y, w.z, w.w);
+        }
+    }
+    __device__ __forceinline__ void put2(const MixedArgs &A, int ch, int, int kba, int kbb, const float *,
+                                         const float *, float2, float2, float2, float2, float, bool va, bool vb)
+    {
+        if (va) one(A.S, ch, iya, kba, za);
+        if (vb && iyb >= 0) one(A.S, ch, iyb, kbb, zb);
     }
 };
 
@@ -1332,9 +1375,9 @@ __device__ __forceinline__ void eval_state(const Smem &sm, const float2 C[NF][kO
 
 // One forward work item (tile x pulse batch) of one scene. Every thread of the
 // CTA calls it; it starts and ends with the CTA's range tiles all zero.
-template <int TAPS, typename OutT, int V, int NCC = 0, bool SH3 = false>
+template <int TAPS, typename OutT, int V, int NCC = 0, bool SH3 = false, typename Sink = ScatterSink<OutT>>
 __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs &P, const ItemGeo &I, int n0, int np,
-                             OutT *iq)
+                             OutT *iq, const ProbeOut *probe = nullptr)
 {
     constexpr int NF = Var<V>::NF;
     const DevScene &S = A.S;
@@ -1363,13 +1406,21 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
     if (Var<V>::LUT) stage_luts(sm, S);
     __syncthreads();
 
-    ScatterSink<OutT> sink;
+    Sink sink;
     sink.stage = sm.stage + warp * SBINS * SROW;
     sink.tiles = sm.tile;
     sink.iq = iq;
     sink.n0 = n0;
     sink.np = np;
     sink.cstride = 2 * (size_t)np * S.nr;
+    if constexpr (Sink::kProbe) {
+        sink.out = *probe;
+        sink.ix = ix;
+        sink.iya = iya;
+        sink.iyb = two ? iyb : -1;
+        if (ga.valid) probe->cells[(size_t)iya * S.nx + ix] = ga.cell;
+        if (two && gb.valid) probe->cells[(size_t)iyb * S.nx + ix] = gb.cell;
+    }
     // pack the two facets: .x = row w, .y = row w + 8 (a copy of .x, masked off, for 8-row tiles)
     PairGeo G;
     const FacetGeo &gq = two ? gb : ga;
@@ -1401,6 +1452,11 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
             }
             G.zr = make_float2(ga.z.x, two ? gb.z.x : 0.0f);
             G.zi = make_float2(ga.z.y, two ? gb.z.y : 0.0f);
+            if constexpr (Sink::kProbe) {
+                sink.epoch = e;
+                sink.za = ga.z;
+                sink.zb = gb.z;
+            }
             for (; n < ne; ++n) {
                 const int pi = n - c0;
                 sink.set_pulse(A, n, n & (kTileBufs - 1));
@@ -1448,6 +1504,20 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     if (I.pa >= I.pe) return;
     clear_smem(sm, A.S.nc);
     forward_item<TAPS, OutT, V, NCC, SH3>(sm, A, P, I, n0, np, iq);
+}
+
+// Index probe: the accumulator's work items with the probe sink (no output is
+// accumulated; see ProbeSink).
+template <int TAPS, int V, int NCC, bool SH3>
+__global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
+    probe_mixed_kernel(MixedArgs A, PolyArgs P, int n0, int np, int b0, ProbeOut out)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Smem sm = carve(smem_raw, A.S.nc, true, Var<V>::NF);
+    const ItemGeo I = item_geo(A, blockIdx.x, b0 + blockIdx.y, TY, n0, np);
+    if (I.pa >= I.pe) return;
+    clear_smem(sm, A.S.nc);
+    forward_item<TAPS, float, V, NCC, SH3, ProbeSink>(sm, A, P, I, n0, np, nullptr, &out);
 }
 
 // Work list of a batched launch: scene s owns items [start[s], start[s + 1]);
@@ -1789,6 +1859,32 @@ cudaError_t accumulate_t(const DevScene &S, const MixedTables &M, cudaStream_t s
     return accumulate_nc<TAPS, OutT, V, 0>(S, M, st, n0, np, iq);
 }
 
+template <int TAPS, int V, int NCC, bool SH3 = false>
+cudaError_t probe_nc(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, const ProbeOut &out)
+{
+    const MixedArgs A = make_args(S, M);
+    const PolyArgs P = make_poly(M);
+    const int bytes = layout(S.nc, true, Var<V>::NF).total;
+    cudaError_t e = prep(probe_mixed_kernel<TAPS, V, NCC, SH3>, bytes);
+    if (e != cudaSuccess) return e;
+    return over_batches(S, M, TY, n0, np, [&](int bb, dim3 grid) {
+        probe_mixed_kernel<TAPS, V, NCC, SH3><<<grid, NT, bytes, st>>>(A, P, n0, np, bb, out);
+        return cudaGetLastError();
+    });
+}
+
+// Same instantiation choice as accumulate_t, so that the probe runs the code of
+// the accumulator the scene uses.
+template <int TAPS, int V>
+cudaError_t probe_t(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, const ProbeOut &out)
+{
+    if constexpr (TAPS == 8) {
+        if (S.nc == 6 && S.rx_share == 0x36u) return probe_nc<TAPS, V, 6, true>(S, M, st, n0, np, out);
+        if (S.nc == 6) return probe_nc<TAPS, V, 6>(S, M, st, n0, np, out);
+    }
+    return probe_nc<TAPS, V, 0>(S, M, st, n0, np, out);
+}
+
 template <int TAPS, typename InT, int V, int NCC, bool SH3 = false>
 cudaError_t adjoint_nc(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, const InT *resid,
                        double *g_sigma, double *g_uv)
@@ -1843,6 +1939,12 @@ struct MixedLaunch {
                                : accumulate_t<8, float, V>(S, M, st, n0, np, (float *)iq);
         return S.taps == 1 ? accumulate_t<1, double, V>(S, M, st, n0, np, (double *)iq)
                            : accumulate_t<8, double, V>(S, M, st, n0, np, (double *)iq);
+    }
+
+    static cudaError_t probe(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np,
+                             const ProbeOut &out)
+    {
+        return S.taps == 1 ? probe_t<1, V>(S, M, st, n0, np, out) : probe_t<8, V>(S, M, st, n0, np, out);
     }
 
     static cudaError_t adjoint(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np,
@@ -1913,6 +2015,17 @@ cudaError_t HARM_CAT(mixed_adjoint_v, HARM_MIXED_VARIANT)(const DevScene &S, con
 cudaError_t HARM_CAT(mixed_batch_v, HARM_MIXED_VARIANT)(const BatchLaunch &L, cudaStream_t st)
 {
     return MixedLaunch<HARM_MIXED_VARIANT>::batch(L, st);
+}
+cudaError_t HARM_CAT(mixed_probe_v, HARM_MIXED_VARIANT)(const DevScene &S, const MixedTables &M, cudaStream_t st,
+                                                        int n0, int np, int *bins, void *speckle, void *words,
+                                                        int *cells)
+{
+    ProbeOut out;
+    out.bins = bins;
+    out.speckle = reinterpret_cast<float2 *>(speckle);
+    out.words = reinterpret_cast<uint4 *>(words);
+    out.cells = cells;
+    return MixedLaunch<HARM_MIXED_VARIANT>::probe(S, M, st, n0, np, out);
 }
 #endif
 

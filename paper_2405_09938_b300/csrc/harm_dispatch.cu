@@ -204,6 +204,8 @@ cudaError_t phasor_tables(harm_scene *s, const WaveSets &W, const PulseState *ps
 
 template cudaError_t phasor_tables<double2>(harm_scene *, const WaveSets &, const PulseState *, const double2 **,
                                             const double2 **, const double2 **);
+template cudaError_t phasor_tables<float2>(harm_scene *, const WaveSets &, const PulseState *, const float2 **,
+                                           const float2 **, const float2 **);
 
 harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps, const WaveSets &W)
 {
@@ -271,7 +273,8 @@ harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps,
 
 cudaError_t launch_generate(harm_scene *s, int n0, int np, void *state)
 {
-    if (s->desc.precision == HARM_PREC_FP64) return launch_generate_f64(s->dev, s->stream, n0, np, (double *)state);
+    if (s->desc.precision != HARM_PREC_MIXED)
+        return launch_generate_plain(s->dev, s->desc.precision == HARM_PREC_FP64, s->stream, n0, np, state);
     return launch_generate_mixed(s->dev, s->mixed, s->stream, n0, np, (float *)state);
 }
 
@@ -282,7 +285,8 @@ cudaError_t launch_accumulate(harm_scene *s, int n0, int np, void *iq, harm_dtyp
 
 cudaError_t launch_accumulate_on(harm_scene *s, cudaStream_t st, int n0, int np, void *iq, harm_dtype dtype)
 {
-    if (s->desc.precision == HARM_PREC_FP64) return launch_accumulate_f64(s->dev, st, n0, np, iq, dtype);
+    if (s->desc.precision != HARM_PREC_MIXED)
+        return launch_accumulate_plain(s->dev, s->desc.precision == HARM_PREC_FP64, st, n0, np, iq, dtype);
     return launch_accumulate_mixed(s->dev, s->mixed, st, n0, np, iq, dtype);
 }
 

@@ -66,6 +66,8 @@ struct DevScene {
     const double2 *ex;          // [nw][nx]   e^{i kx x}
     const double2 *ey;          // [nw][ny]   a e^{i phi} e^{i ky y}
     const double2 *tt;          // [nw][np_total] e^{-i omega t_s}
+    // the same tables in float (FP32 plain path)
+    const float2 *ex32, *ey32, *tt32;
     unsigned int *flags;        // device error / overflow counters [4]
     // variants of Sec. III
     int cwm;                    // Choppy Wave Model: 8 state fields instead of 3

@@ -89,9 +89,12 @@ cudaError_t launch_accumulate_on(harm_scene *s, cudaStream_t st, int n0, int np,
 cudaError_t launch_adjoint(harm_scene *s, int n0, int np, const void *resid, harm_dtype dtype, double *g_sigma0,
                            double *g_uv);
 
-// FP64 path
-cudaError_t launch_generate_f64(const DevScene &S, cudaStream_t st, int n0, int np, double *state);
-cudaError_t launch_accumulate_f64(const DevScene &S, cudaStream_t st, int n0, int np, void *iq, harm_dtype dtype);
+// plain paths (every per-facet step in double, fp64 = true, or in float)
+cudaError_t launch_generate_plain(const DevScene &S, bool fp64, cudaStream_t st, int n0, int np, void *state);
+cudaError_t launch_accumulate_plain(const DevScene &S, bool fp64, cudaStream_t st, int n0, int np, void *iq,
+                                    harm_dtype dtype);
+cudaError_t launch_probe_plain(const DevScene &S, bool fp64, cudaStream_t st, int n0, int np, int *bins,
+                               void *speckle, void *words, int *cells);
 // mixed path
 cudaError_t launch_generate_mixed(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np,
                                   float *state);
@@ -119,6 +122,9 @@ bool batch_share3(const harm_scene *s);  // 6 channels in two antennas of 3 phas
 int batch_ctas(int device, int variant);
 cudaError_t batch_launch(const BatchLaunch &L, cudaStream_t st);
 
+// Index probe of the mixed accumulator (see harm_probe_indices).
+cudaError_t launch_probe_mixed(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np, int *bins,
+                               void *speckle, void *words, int *cells);
 cudaError_t launch_adjoint_mixed(const DevScene &S, const MixedTables &M, cudaStream_t st, int n0, int np,
                                  const void *resid, harm_dtype dtype, double *g_sigma, double *g_uv);
 

@@ -243,7 +243,7 @@ harm_status validate(const harm_scene_desc *d)
     if (d->epoch_pulses < 0) return fail(HARM_E_INVALID, "epoch_pulses must be >= 0");
     if (d->taps != 1 && d->taps != 8) return fail(HARM_E_UNSUPPORTED, "taps must be 1 or 8");
     if (!(d->kaiser_beta >= 0 && d->kaiser_beta <= 20)) return fail(HARM_E_INVALID, "kaiser_beta must be in [0, 20]");
-    if (d->precision != HARM_PREC_FP64 && d->precision != HARM_PREC_MIXED)
+    if (d->precision != HARM_PREC_FP64 && d->precision != HARM_PREC_MIXED && d->precision != HARM_PREC_FP32)
         return fail(HARM_E_INVALID, "unknown precision %d", d->precision);
     const harm_antenna *ants[1 + HARM_MAX_CHANNELS];
     ants[0] = &d->tx;
@@ -524,7 +524,7 @@ harm_status harm_scene_set_pattern(harm_scene *s, int32_t antenna, int32_t nu, i
         L.v0 = v0;
         L.inv_dv = 1.0 / dv;
         void *p = nullptr;
-        if (s->desc.precision == HARM_PREC_FP64) {
+        if (s->desc.precision != HARM_PREC_MIXED) {  // the plain paths read the grid in double
             HARM_CUDA(cudaMalloc(&p, nn * sizeof(double2)), "cudaMalloc u-v grid");
             cudaError_t e = cudaMemcpy(p, gain_host, nn * sizeof(double2), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) {
@@ -607,6 +607,27 @@ harm_status harm_echo_adjoint(harm_scene *s, int32_t n0, int32_t np, const void 
     cudaError_t e = harm::launch_adjoint(s, n0, np, resid_dev, dtype, grad_sigma0_dev, grad_uv_dev);
     if (e == cudaErrorNotSupported) return fail(HARM_E_UNSUPPORTED, "adjoint not available for this scene");
     if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+    return HARM_OK;
+}
+
+harm_status harm_probe_indices(harm_scene *s, int32_t n0, int32_t np, int32_t *bins_dev, void *speckle_dev,
+                               uint32_t *words_dev, int32_t *cells_dev)
+{
+    harm_status st = check_window(s, n0, np);
+    if (st != HARM_OK) return st;
+    if ((st = check_device(s)) != HARM_OK) return st;
+    if (np == 0) return HARM_OK;
+    const bool fp64 = s->desc.precision == HARM_PREC_FP64;
+    const size_t nf = (size_t)s->nf, npl = (size_t)np;
+    if ((st = check_ptr(bins_dev, npl * s->desc.n_channels * nf * 4, "bins_dev")) != HARM_OK) return st;
+    if ((st = check_ptr(speckle_dev, npl * nf * (fp64 ? 16 : 8), "speckle_dev")) != HARM_OK) return st;
+    if ((st = check_ptr(words_dev, npl * nf * 16, "words_dev")) != HARM_OK) return st;
+    if ((st = check_ptr(cells_dev, nf * 4, "cells_dev")) != HARM_OK) return st;
+    cudaError_t e =
+        s->desc.precision == HARM_PREC_MIXED
+            ? harm::launch_probe_mixed(s->dev, s->mixed, s->stream, n0, np, bins_dev, speckle_dev, words_dev, cells_dev)
+            : harm::launch_probe_plain(s->dev, fp64, s->stream, n0, np, bins_dev, speckle_dev, words_dev, cells_dev);
+    if (e != cudaSuccess) return cuda_fail(e, "index probe launch");
     return HARM_OK;
 }
 
@@ -774,6 +795,8 @@ harm_status build_scene_tables(harm_scene *s)
     }
     if (d.precision == HARM_PREC_FP64)
         HARM_CUDA(phasor_tables<double2>(s, W, v.pulses, &v.ex, &v.ey, &v.tt), "wave phasor tables");
+    if (d.precision == HARM_PREC_FP32)
+        HARM_CUDA(phasor_tables<float2>(s, W, v.pulses, &v.ex32, &v.ey32, &v.tt32), "wave phasor tables");
     std::vector<unsigned int> flags(4, 0u);
     const unsigned int *fl = nullptr;
     if ((st = upload(s, flags, &fl)) != HARM_OK) return st;

@@ -19,7 +19,7 @@ HARM_ABI_VERSION = 2
 HARM_MAX_CHANNELS = 16
 HARM_OK, HARM_E_INVALID, HARM_E_CUDA, HARM_E_OOM, HARM_E_TIMEOUT, HARM_E_UNSUPPORTED = range(6)
 HARM_C64, HARM_C128 = 0, 1
-HARM_PREC_FP64, HARM_PREC_MIXED = 0, 1
+HARM_PREC_FP64, HARM_PREC_MIXED, HARM_PREC_FP32 = 0, 1, 2
 STATUS_NAMES = {0: "HARM_OK", 1: "HARM_E_INVALID", 2: "HARM_E_CUDA", 3: "HARM_E_OOM",
                 4: "HARM_E_TIMEOUT", 5: "HARM_E_UNSUPPORTED"}
 
@@ -94,6 +94,7 @@ SIGNATURES = {
     "harm_batch_run": (C.c_int, [_VP, C.POINTER(_VP), C.c_int32]),
     "harm_batch_destroy": (C.c_int, [_VP]),
     "harm_batch_run_noalloc": (C.c_int, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP), C.c_int32]),
+    "harm_probe_indices": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP, _VP, _VP, _VP]),
     "harm_last_error": (C.c_char_p, []),
 }
 
@@ -284,7 +285,7 @@ def _dev_ptr(t, what, size=None, dtype=None):
         raise HarmError(HARM_E_INVALID, "%s must be %s, not %s" % (what, dtype, t.dtype))
     if size is not None:
         scene, numel = size
-        if t.numel() != numel:
+        if numel > 0 and t.numel() != numel:
             raise HarmError(HARM_E_INVALID, "%s holds %d elements, the call needs %d" % (what, t.numel(), numel))
         if scene.device >= 0 and t.device.index != scene.device:
             raise HarmError(HARM_E_INVALID, "%s is on cuda:%s, the scene on cuda:%d"
@@ -353,7 +354,7 @@ def harm_echo_accumulate_host(scene: Scene, n0: int, np_: int, iq_host, block_pu
         raise HarmError(HARM_E_INVALID, "iq_host must be a CPU tensor")
     if not iq_host.is_contiguous():
         raise HarmError(HARM_E_INVALID, "iq_host must be contiguous")
-    if iq_host.numel() != _iq_numel(scene, np_):
+    if np_ > 0 and iq_host.numel() != _iq_numel(scene, np_):
         raise HarmError(HARM_E_INVALID, "iq_host holds %d elements, the call needs %d"
                         % (iq_host.numel(), _iq_numel(scene, np_)))
     _check(load_library().harm_echo_accumulate_host(scene.handle, n0, np_, C.c_void_p(iq_host.data_ptr()),
@@ -373,6 +374,27 @@ def harm_echo_adjoint(scene: Scene, n0: int, np_: int, resid, grad_sigma0=None, 
     gs = _dev_ptr(grad_sigma0, "grad_sigma0", (scene, nce), torch.float64) if grad_sigma0 is not None else None
     gu = _dev_ptr(grad_uv, "grad_uv", (scene, 2 * nce), torch.float64) if grad_uv is not None else None
     _check(load_library().harm_echo_adjoint(scene.handle, n0, np_, rp, _dtype_code(resid), gs, gu))
+
+
+def harm_probe_indices(scene: Scene, n0: int, np_: int):
+    """Integer work of the accumulator for pulses [n0, n0 + np_) (see
+    include/harm.h): returns CUDA tensors bins [np_, n_channels, ny, nx] int32,
+    speckle [np_, ny, nx] (complex128 for FP64 scenes, complex64 otherwise),
+    words [np_, ny, nx, 4] int32 (the uint32 Philox words, reinterpreted) and
+    cells [ny, nx] int32."""
+    import torch
+    d = scene.desc
+    nc, nx, ny = len(d["rx"]), d["nx"], d["ny"]
+    dev = torch.device("cuda", scene.device)
+    bins = torch.empty((np_, nc, ny, nx), dtype=torch.int32, device=dev)
+    sdt = torch.complex128 if scene.precision == HARM_PREC_FP64 else torch.complex64
+    spk = torch.empty((np_, ny, nx), dtype=sdt, device=dev)
+    words = torch.empty((np_, ny, nx, 4), dtype=torch.int32, device=dev)
+    cells = torch.empty((ny, nx), dtype=torch.int32, device=dev)
+    _check(load_library().harm_probe_indices(scene.handle, n0, np_, C.c_void_p(bins.data_ptr()),
+                                             C.c_void_p(spk.data_ptr()), C.c_void_p(words.data_ptr()),
+                                             C.c_void_p(cells.data_ptr())))
+    return bins, spk, words, cells
 
 
 def harm_scene_sync(scene: Scene):

@@ -32,6 +32,16 @@ def run_states(desc, precision, n0, np_):
     return out
 
 
+def take_pulses(iq, pulses):
+    """Pulse rows [:, pulses, :] of an IQ tensor on the device, as a numpy array.
+    The indices are checked on the host first: an out-of-range index into a CUDA
+    tensor would trip a device-side assert and lose the context."""
+    n = iq.shape[1]
+    bad = [p for p in pulses if not 0 <= p < n]
+    assert not bad, "pulses %s outside [0, %d)" % (bad, n)
+    return iq[:, list(pulses), :].cpu().numpy()
+
+
 def rel_rms(got, want):
     num = np.sum(np.abs(got - want) ** 2)
     den = np.sum(np.abs(want) ** 2)

@@ -17,7 +17,7 @@ import pytest
 import harm_scenes as hs
 import oracle
 from paper_2405_09938_b300 import harm
-from tests.gpu_util import assert_iq, ati_phase_bias, rel_rms
+from tests.gpu_util import assert_iq, ati_phase_bias, rel_rms, take_pulses
 
 pytestmark = pytest.mark.gpu
 
@@ -39,7 +39,7 @@ def test_headline_scene_full_burst_sampled_pulses():
     harm.harm_echo_accumulate(sc, 0, d["n_pulses"], iq)
     harm.harm_scene_sync(sc)
     pulses = [0, 1023, 2047]
-    got = iq[:, pulses, :].cpu().numpy()
+    got = take_pulses(iq, pulses)
     sc.close()
     del iq
     want = oracle.echo(d, pulses)
@@ -49,6 +49,34 @@ def test_headline_scene_full_burst_sampled_pulses():
         assert_iq(got[c], want[c], TOL_MIXED)
     for a, b in ((0, 1), (1, 2), (3, 4), (4, 5)):
         assert abs(ati_phase_bias(got, want, a, b)) < 1e-4
+
+
+def test_headline_scene_plain_fp32_error():
+    """The plain method in FP32 (HARM_PREC_FP32) on the full headline scene, one
+    launch over the burst: its IQ error against the FP64 oracle on sampled pulses,
+    recorded to show why the mixed path keeps the reference ranges in FP64. FP32
+    rounding of the ~2 km range offsets (1.2e-4 m) and of the ~2e5 rad phase
+    (1.6e-2 rad) spreads every contribution's phase by ~1e-2 rad, so the IQ error
+    is ~1e-2 (measured on a B300: 5.4e-3, worst ATI bias 4.6e-4 rad): two orders
+    above the mixed path on the same scene."""
+    import torch
+    d = hs.ati_scene()
+    sc = harm.harm_scene_create(d, harm.HARM_PREC_FP32)
+    iq = torch.zeros((6, d["n_pulses"], d["n_range"]), dtype=torch.complex64, device="cuda")
+    harm.harm_echo_accumulate(sc, 0, d["n_pulses"], iq)
+    harm.harm_scene_sync(sc)
+    pulses = [0, 1023, 2047]
+    got = take_pulses(iq, pulses)
+    sc.close()
+    del iq
+    want = oracle.echo(d, pulses)
+    err = rel_rms(got, want)
+    bias = max(abs(ati_phase_bias(got, want, a, b)) for a, b in ((0, 1), (1, 2), (3, 4), (4, 5)))
+    print("headline scene, plain FP32: IQ rel RMS %.3e, worst ATI bias %.3e rad" % (err, bias))
+    assert err < 2e-2
+    assert bias < 5e-3
+    # the plain FP32 form cannot hold the mixed path's 1e-4 bound on this scene
+    assert err > 10 * TOL_MIXED
 
 
 def test_headline_complex64_accumulation_error():
@@ -64,7 +92,7 @@ def test_headline_complex64_accumulation_error():
         iq = torch.zeros((6, d["n_pulses"], d["n_range"]), dtype=dt, device="cuda")
         harm.harm_echo_accumulate(sc, 0, d["n_pulses"], iq)
         harm.harm_scene_sync(sc)
-        outs.append(iq[:, pulses, :].cpu().numpy().astype(np.complex128))
+        outs.append(take_pulses(iq, pulses).astype(np.complex128))
         del iq
     sc.close()
     err = rel_rms(outs[0], outs[1])
@@ -85,7 +113,7 @@ def test_batch_of_48_scenes_full_size_sampled():
     for s in (int(np.argmin(sizes)), int(np.argmax(sizes))):
         d = descs[s]
         n = d["n_pulses"] // 3
-        got = iqs[s][:, [n], :].cpu().numpy()
+        got = take_pulses(iqs[s], [n])
         want = oracle.echo(d, [n])
         err, pe = assert_iq(got, want, TOL_MIXED)
         print("batch scene %d (%d facets): IQ rel RMS %.3e, per-element %.3e" % (s, sizes[s], err, pe))

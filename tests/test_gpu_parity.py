@@ -77,6 +77,34 @@ def test_fp64_path_c64_output():
     assert_iq(got, want, 1e-6)
 
 
+# ------------------------------------------------------------------ plain FP32 path
+def test_wave_scene_fp32_plain_error():
+    """The plain method in FP32: same kernel structure as the FP64 path, every
+    per-facet step in float. Its error is set by FP32 rounding of the range offsets
+    and of the phase K0 (r - R) over this 96 x 80 m patch (measured on a B300:
+    2.2e-4); the bound below is that figure with margin, not the mixed path's."""
+    d = small_wave_scene()
+    got = run_echo(d, harm.HARM_PREC_FP32, 0, 64, "c64")
+    want = oracle.echo(d, list(range(64)))
+    err = rel_rms(got, want)
+    print("small wave scene, plain FP32: IQ rel RMS %.3e" % err)
+    assert err < 1e-3
+
+
+def test_fp32_plain_states_and_window():
+    # the plain FP32 generator against the oracle's states, and a ragged grid with
+    # an unaligned pulse window through the FP32 accumulator (c128 output)
+    d = small_wave_scene(n_pulses=100, nx=45, ny=19)
+    got = run_states(d, harm.HARM_PREC_FP32, 30, 4)
+    for i, n in enumerate(range(30, 34)):
+        want = oracle.facet_states(d, n)
+        assert np.abs(got[i] - want).max() < 2e-5
+    n0, np_ = 41, 23
+    got = run_echo(d, harm.HARM_PREC_FP32, n0, np_, "c128")
+    want = oracle.echo(d, list(range(n0, n0 + np_)))
+    assert rel_rms(got, want) < 1e-3
+
+
 # ------------------------------------------------------------------ mixed path
 @pytest.mark.parametrize("taps", [8, 1])
 def test_static_patch_mixed(taps):

@@ -579,3 +579,34 @@ def test_wave_scene_bins_and_energy():
     x, y = kin.facet_xy(d, f)
     s = oracle.surface(tab, float(x), float(y), g["ts"])
     assert np.allclose(states[:, 17, 5], s, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Bulk exports used by the GPU index parity: the same quantities as the pinned
+# single-facet and single-draw functions
+# ---------------------------------------------------------------------------
+def test_bin_positions_are_the_contributions_positions():
+    d = hs.ati_scene(n_pulses=64, nx=24, ny=13, n_range=1024)
+    d["cells"] = {"ncx": 5, "ncy": 3, "cell_m": 10.0, "sigma0": np.full((3, 5), 0.02),
+                  "uv": np.zeros((3, 5, 2))}
+    p, cells = oracle.bin_positions(d, [3, 40])
+    nx = d["nx"]
+    for i, n in enumerate((3, 40)):
+        st = oracle.facet_states(d, n)
+        for c in (0, 4):
+            for f in (0, 7, nx + 3, 13 * nx - 1):
+                _, pf = oracle.contribution(d, n, c, f, st[:, f // nx, f % nx] if st.ndim == 3 else st[:, f])
+                assert p[i, c, f // nx, f % nx] == pf
+    # cells of 10 m on 2 m facets: 5 facets per cell, clamped at the far edges
+    assert cells[0, 0] == 0 and cells[0, 4] == 0 and cells[0, 5] == 1
+    assert cells[0, nx - 1] == 4 and cells[12, 0] == 2 * 5
+
+
+def test_speckle_words_match_curand():
+    seed = 1
+    facets = [0, 3, 77, 123457, 2**32 - 1]
+    epochs = [0, 5, 60, 61, 7]
+    got = oracle.speckle_words(seed, facets, epochs)
+    for q, (f, e) in enumerate(zip(facets, epochs)):
+        blk = _curand_blocks(seed, f * 65536 + e, 1)[0]
+        assert [int(v) for v in got[q]] == [int(v) for v in blk]
