@@ -16,6 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libharm.so")
+PEAKS_LIB = os.path.join(HERE, "libharm_peaks.so")  # arithmetic-pipe microbenchmarks (include/harm_peaks.h)
 SOURCES = ["harm_scene.cu", "harm_dispatch.cu", "harm_batch.cu", "harm_noalloc.cu", "harm_host.cu", "echo_plain.cu",
            "echo_mixed.cu",
            "echo_mixed_cwm.cu", "echo_mixed_lut.cu", "echo_mixed_cwm_lut.cu"]
@@ -30,19 +31,36 @@ def nvcc_path() -> str:
 
 
 def _deps():
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f != "peaks.cu"]
     files.append(os.path.join(INCLUDE, "harm.h"))
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB, deps=None) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(f) <= t for f in _deps())
+    t = os.path.getmtime(lib)
+    return all(os.path.getmtime(f) <= t for f in (deps if deps is not None else _deps()))
+
+
+def build_peaks(force: bool = False) -> str:
+    """Build libharm_peaks.so (one translation unit, no dependence on libharm)."""
+    deps = [os.path.join(CSRC, "peaks.cu"), os.path.join(INCLUDE, "harm_peaks.h")]
+    if not force and up_to_date(PEAKS_LIB, deps):
+        return PEAKS_LIB
+    tmp = PEAKS_LIB + ".tmp%d" % os.getpid()
+    cmd = [nvcc_path(), "-shared", os.path.join(CSRC, "peaks.cu"), "-o", tmp] + ARCH + [
+        "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        sys.stderr.write(r.stdout + r.stderr)
+        raise RuntimeError("nvcc failed on peaks.cu")
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    build_peaks(force)
     if not force and up_to_date():
         return LIB
     nvcc = nvcc_path()

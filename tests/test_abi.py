@@ -224,3 +224,20 @@ def test_binding_refuses_wrong_sized_or_misplaced_buffers():
     with pytest.raises(harm.HarmError) as e:
         harm.harm_echo_accumulate(sc, 0, 4, _fake((nc, 4, nr), torch.complex64))
     assert "cuda:1" in str(e.value)
+
+
+def test_peaks_library_exports_its_header():
+    lib = ctypes.CDLL(harm_build.build_peaks())
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "harm_peaks.h")).read(), flags=re.S)
+    names = sorted(set(re.findall(r"\b(harm_peak_[a-z_]+)\s*\(", src)))
+    assert names == ["harm_peak_launch", "harm_peak_ops"]
+    for name in names:
+        assert hasattr(lib, name), name
+    from paper_2405_09938_b300 import peaks
+    pl = peaks.load_library()
+    # operation counts of a launch: blocks x 256 threads x 8 chains x iterations
+    assert pl.harm_peak_ops(0, 2, 3) == 2 * 2 * 256 * 8 * 3
+    assert pl.harm_peak_ops(1, 2, 3) == 4 * 2 * 256 * 8 * 3
+    assert pl.harm_peak_ops(3, 1, 1) == 256 * 8
+    assert pl.harm_peak_ops(9, 1, 1) == 0
+    assert pl.harm_peak_launch(0, 0, 1, None, None) == 1  # bad arguments: refused before any launch
