@@ -656,8 +656,11 @@ def measure_adjoint(args, stream, flush):
 def measure_batched(args, stream):
     """48 uneven scenes (0.5 x 0.5 km .. 8 x 4 km, 256 .. 2048 pulses, 1024 .. 8192
     range samples, 6 channels each) as one persistent launch replayed from a CUDA
-    graph, after the autotuner picked the tile heights. One untimed warm-up run,
-    then the median of five timed replays (device time by CUDA events)."""
+    graph, after the autotuner picked the launch shape (tile rows and time-Taylor
+    window per size class, CTAs per SM). One untimed warm-up run, then the median
+    of five timed replays (device time by CUDA events); then the same with the
+    fixed default shape (16-row tiles, full windows, 2 CTAs per SM) for the
+    tuner's gain."""
     import torch
     from paper_2405_09938_b300 import harm
     descs = hs.batch_scenes()
@@ -670,18 +673,27 @@ def measure_batched(args, stream):
     t0 = time.perf_counter()
     harm.harm_batch_tune(b, iqs)
     tune_s = time.perf_counter() - t0
-    rows = harm.harm_batch_tile_rows(b)
-    harm.harm_batch_run(b, iqs)
-    torch.cuda.synchronize()
-    reps = []
-    for _ in range(5):
-        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+    cfg = harm.harm_batch_config(b)
+    rows = cfg["rows"]
+
+    def replays(k):
         harm.harm_batch_run(b, iqs)
-        e.record(stream)
         torch.cuda.synchronize()
-        reps.append(a.elapsed_time(e))
+        out = []
+        for _ in range(k):
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            harm.harm_batch_run(b, iqs)
+            e.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(e))
+        return out
+
+    reps = replays(5)
     ms = statistics.median(reps)
+    pb = harm.harm_scene_query(scenes[0])["pulse_batch"]
+    harm.harm_batch_set_config(b, [16] * len(descs), [pb] * len(descs), 2)
+    default_ms = statistics.median(replays(3))
     units = sum(hs.n_contributions(d) for d in descs)
     b.close()
     for sc in scenes:
@@ -691,6 +703,8 @@ def measure_batched(args, stream):
     return {"workload": "batch_48_uneven_scenes_6ch", "scenes": len(descs), "contributions": units,
             "ms": ms, "ms_replays": reps, "value": units / (ms * 1e-3), "launches": 1, "graph": True,
             "tile_rows": {"8": rows.count(8), "16": rows.count(16)},
+            "windows": {str(w): cfg["windows"].count(w) for w in sorted(set(cfg["windows"]))},
+            "ctas_per_sm": cfg["ctas_per_sm"], "default_shape_ms": default_ms, "tuner_gain": default_ms / ms,
             "scene_create_s": create_s, "tune_s": tune_s}
 
 

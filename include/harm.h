@@ -246,11 +246,32 @@ typedef struct harm_batch harm_batch; /* opaque, owned by the library */
    HARM_E_UNSUPPORTED (an FP64 scene), HARM_E_OOM, HARM_E_CUDA. */
 harm_status harm_batch_create(harm_scene *const *scenes, int32_t n_scenes, harm_batch **out);
 
-/* Autotuner: times the persistent launch with tile heights of 8 and 16 facet rows
-   on the first pulse batches of each scene-size class and keeps the faster per
-   class. iq_dev[s] are the scenes' complex64 IQ buffers [n_channels][n_pulses]
-   [n_range] (device); their contents are overwritten. Synchronous. */
+/* Autotuner of the launch shape. Per scene-size class (fewer than 1e6 facets,
+   fewer than 4e6, more) it times the persistent launch on the first 256 pulses
+   of the class's two largest scenes with each tile height (16 or 8 facet rows)
+   and each time-Taylor window (harm_scene_info.pulse_batch pulses per work item,
+   or half of it) -- 1 untimed and 3 timed launches per candidate, median -- and
+   keeps the fastest; then it times the launch over all classes' samples with 2
+   and 1 CTAs per SM (1 only for the Choppy Wave Model) and keeps the faster. The
+   choices are remembered for the life of the process per (device, surface model
+   and pattern kind, channel count, taps, channel layout, size class), so a later
+   batch of the same kind is configured without timing. The tile width (32
+   facets, the warp's lanes) is fixed. iq_dev[s] are the scenes' complex64 IQ
+   buffers [n_channels][n_pulses][n_range] (device); their contents are
+   overwritten. Synchronous. */
 harm_status harm_batch_tune(harm_batch *batch, void *const *iq_dev);
+
+/* The launch shape in use: tile rows and pulses per work item of each scene
+   (rows[n_scenes], windows[n_scenes], host memory; either may be NULL) and the
+   CTAs per SM of the launch (may be NULL). */
+harm_status harm_batch_config(const harm_batch *batch, int32_t *rows, int32_t *windows, int32_t *ctas_per_sm);
+
+/* Pin the launch shape instead of tuning: rows[s] 8 or 16, windows[s] the
+   scene's pulse_batch or half of it, ctas_per_sm 1 or 2 (1 for the Choppy Wave
+   Model). The next harm_batch_run captures its graph again. Synchronous with
+   respect to the batch's earlier launches. Errors: HARM_E_INVALID. */
+harm_status harm_batch_set_config(harm_batch *batch, const int32_t *rows, const int32_t *windows,
+                                  int32_t ctas_per_sm);
 
 /* Tile heights chosen for each scene (rows[n_scenes], host memory). */
 harm_status harm_batch_tile_rows(const harm_batch *batch, int32_t *rows);

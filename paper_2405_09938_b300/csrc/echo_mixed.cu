@@ -79,10 +79,21 @@ int mixed_batch_pulses() { return NBG; }
 // ---------------------------------------------------------------------------
 size_t batch_args_bytes() { return sizeof(MixedArgs); }
 
-void batch_fill_args(const harm_scene *s, void *dst)
+void batch_fill_args(const harm_scene *s, void *dst, int window)
 {
     MixedArgs A = make_args(s->dev, s->mixed);
+    if (window == s->mixed.alt_nb) {
+        A.tc = s->mixed.alt_tc;
+        A.tau = s->mixed.alt_tau;
+        A.nb = s->mixed.alt_nb;
+        A.n_batches = s->mixed.alt_n_batches;
+    }
     memcpy(dst, &A, sizeof(MixedArgs));
+}
+
+int batch_windows(const harm_scene *s, int window)
+{
+    return window == s->mixed.alt_nb ? s->mixed.alt_n_batches : s->mixed.n_batches;
 }
 
 int batch_tiles(const harm_scene *s, int ty)

@@ -1,11 +1,15 @@
-// Batched scenes: work list, project-written autotuner of the tile height, and
-// CUDA-graph capture / replay of the persistent batched launch.
+// Batched scenes: work list, project-written autotuner of the launch shape (tile
+// height and time-Taylor window per scene-size class, CTAs per SM for the
+// launch), and CUDA-graph capture / replay of the persistent batched launch.
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "harm.h"
@@ -26,7 +30,10 @@ struct harm_batch {
     int variant = 0;
     int share3 = 0;
     int ctas = 0;
+    int sms = 0;                // SMs of the device
+    int ctas_per_sm = 2;
     std::vector<int> ty;        // tile rows by scene
+    std::vector<int> win;       // pulses per work item by scene (time-Taylor window)
     std::vector<int> order;     // processing order (largest first)
     std::vector<void *> allocs;
     void *d_args = nullptr;
@@ -77,6 +84,25 @@ int size_class(const harm_scene *s)
     return nf < 1e6 ? 0 : (nf < 4e6 ? 1 : 2);
 }
 
+// Choices of the autotuner, kept for the life of the process: per (device,
+// per-pulse code variant, channel count, taps, channel layout, size class) the
+// tile height and window; per (the same without the class, plus the classes
+// present) the CTAs per SM of the launch.
+struct TuneKey {
+    int device, variant, nc, taps, share3, cls;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(device, variant, nc, taps, share3, cls) <
+               std::tie(o.device, o.variant, o.nc, o.taps, o.share3, o.cls);
+    }
+};
+struct ClassChoice {
+    int ty, win;
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, ClassChoice> g_class_choice;
+std::map<TuneKey, int> g_ctas_choice;  // cls = bit mask of the classes present
+
 template <typename T>
 harm_status dalloc(harm_batch *b, T **p, size_t count)
 {
@@ -87,10 +113,10 @@ harm_status dalloc(harm_batch *b, T **p, size_t count)
     return HARM_OK;
 }
 
-// Work list for the current tile heights, limited to the first max_batches pulse
-// batches of each scene (max_batches <= 0: all), restricted to scenes with
-// use[s] set. Uploads start / tiles / ty / order.
-harm_status plan(harm_batch *b, int max_batches, const std::vector<char> &use, int *total)
+// Work list for the current tile heights and windows, limited to the work items
+// that cover the first max_pulses pulses of each scene (max_pulses <= 0: all),
+// restricted to scenes with use[s] set. Uploads start / tiles / ty / order.
+harm_status plan(harm_batch *b, int max_pulses, const std::vector<char> &use, int *total)
 {
     const int n = (int)b->scenes.size();
     std::vector<int> start(n + 1, 0), tiles(n, 0);
@@ -98,8 +124,8 @@ harm_status plan(harm_batch *b, int max_batches, const std::vector<char> &use, i
     for (int k = 0; k < n; ++k) {
         int s = b->order[k];
         const harm_scene *sc = b->scenes[s];
-        int nb = sc->mixed.n_batches;
-        if (max_batches > 0) nb = std::min(nb, max_batches);
+        int nb = harm::batch_windows(sc, b->win[s]);
+        if (max_pulses > 0) nb = std::min(nb, (max_pulses + b->win[s] - 1) / b->win[s]);
         long long items = use[s] ? (long long)tiles[s] * nb : 0;
         if ((long long)start[k] + items > 0x7fffffffll) return fail(HARM_E_INVALID, "batch has more than 2^31 work items");
         start[k + 1] = start[k] + (int)items;
@@ -127,7 +153,7 @@ harm::BatchLaunch launch_desc(harm_batch *b, int total)
     L.total = total;
     L.nc = b->nc;
     L.taps = b->taps;
-    L.ctas = b->ctas;
+    L.ctas = b->ctas_per_sm * b->sms;
     L.variant = b->variant;
     L.share3 = b->share3;
     return L;
@@ -151,6 +177,46 @@ harm_status set_outputs(harm_batch *b, void *const *iq)
     }
     BCUDA(cudaMemcpyAsync(b->d_iq, iq, n * sizeof(void *), cudaMemcpyHostToDevice, b->stream), "upload outputs");
     BCUDA(cudaStreamSynchronize(b->stream), "upload outputs");
+    return HARM_OK;
+}
+
+// Scenes whose window changes get their launch arguments rebuilt and uploaded.
+harm_status set_windows(harm_batch *b, const std::vector<int> &win)
+{
+    const size_t ab = harm::batch_args_bytes();
+    std::vector<unsigned char> tmp(ab);
+    for (size_t s = 0; s < b->scenes.size(); ++s) {
+        if (win[s] == b->win[s]) continue;
+        b->win[s] = win[s];
+        harm::batch_fill_args(b->scenes[s], tmp.data(), win[s]);
+        BCUDA(cudaMemcpyAsync((unsigned char *)b->d_args + ab * s, tmp.data(), ab, cudaMemcpyHostToDevice, b->stream),
+              "upload scene arguments");
+        BCUDA(cudaStreamSynchronize(b->stream), "upload scene arguments");
+    }
+    return HARM_OK;
+}
+
+// Median device time of `reps` launches (after one untimed) over the work items
+// of the first max_pulses pulses of the scenes in `use`.
+harm_status time_sample(harm_batch *b, int max_pulses, const std::vector<char> &use, int reps, cudaEvent_t e0,
+                        cudaEvent_t e1, float *ms_out)
+{
+    int total = 0;
+    harm_status st = plan(b, max_pulses, use, &total);
+    if (st != HARM_OK) return st;
+    std::vector<float> ms;
+    for (int rep = 0; rep <= reps; ++rep) {
+        BCUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), b->stream), "memset");
+        BCUDA(cudaEventRecord(e0, b->stream), "event");
+        BCUDA(harm::batch_launch(launch_desc(b, total), b->stream), "batched launch");
+        BCUDA(cudaEventRecord(e1, b->stream), "event");
+        BCUDA(cudaEventSynchronize(e1), "event");
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0) ms.push_back(t);
+    }
+    std::sort(ms.begin(), ms.end());
+    *ms_out = ms[ms.size() / 2];
     return HARM_OK;
 }
 
@@ -206,7 +272,11 @@ harm_status harm_batch_create(harm_scene *const *scenes, int32_t n, harm_batch *
     for (int s = 0; s < n; ++s)
         if (!harm::batch_share3(scenes[s])) b->share3 = 0;
     b->ctas = harm::batch_ctas(b->device, b->variant);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    b->ctas_per_sm = b->sms > 0 ? std::max(1, b->ctas / b->sms) : 2;
     b->ty.assign(n, 16);
+    b->win.resize(n);
+    for (int s = 0; s < n; ++s) b->win[s] = scenes[s]->mixed.nb;
     b->order.resize(n);
     for (int s = 0; s < n; ++s) b->order[s] = s;
     std::stable_sort(b->order.begin(), b->order.end(),
@@ -214,7 +284,7 @@ harm_status harm_batch_create(harm_scene *const *scenes, int32_t n, harm_batch *
     harm_status st;
     size_t ab = harm::batch_args_bytes();
     std::vector<unsigned char> args(ab * n);
-    for (int s = 0; s < n; ++s) harm::batch_fill_args(b->scenes[s], args.data() + ab * s);
+    for (int s = 0; s < n; ++s) harm::batch_fill_args(b->scenes[s], args.data() + ab * s, b->win[s]);
     unsigned char *d_args = nullptr;
     if ((st = dalloc(b, &d_args, args.size())) != HARM_OK ||
         (st = dalloc(b, &b->d_start, n + 1)) != HARM_OK || (st = dalloc(b, &b->d_tiles, n)) != HARM_OK ||
@@ -267,46 +337,117 @@ harm_status harm_batch_tune(harm_batch *b, void *const *iq)
     if (st != HARM_OK) return st;
     drop_graph(b);
     const int n = (int)b->scenes.size();
-    cudaEvent_t e0, e1;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     BCUDA(cudaEventCreate(&e0), "event");
     BCUDA(cudaEventCreate(&e1), "event");
-    const int cand[2] = {16, 8};
-    for (int cls = 0; cls < 3; ++cls) {
+    // the sample a candidate is timed on: the first kSamplePulses pulses of the
+    // (at most kSampleScenes) largest scenes of the class
+    const int kSamplePulses = 256, kSampleScenes = 2, kReps = 3;
+    std::vector<char> sample_all(n, 0);
+    int class_mask = 0;
+    for (int cls = 0; cls < 3 && st == HARM_OK; ++cls) {
+        std::vector<int> members;
+        for (int k = 0; k < n; ++k)
+            if (size_class(b->scenes[b->order[k]]) == cls) members.push_back(b->order[k]);  // largest first
+        if (members.empty()) continue;
+        class_mask |= 1 << cls;
         std::vector<char> use(n, 0);
-        bool any = false;
-        for (int s = 0; s < n; ++s)
-            if (size_class(b->scenes[s]) == cls) use[s] = 1, any = true;
-        if (!any) continue;
-        float best = 1e30f;
-        int best_ty = 16;
-        for (int c = 0; c < 2; ++c) {
-            for (int s = 0; s < n; ++s)
-                if (use[s]) b->ty[s] = cand[c];
-            int total = 0;
-            if ((st = plan(b, 2, use, &total)) != HARM_OK) break;
-            float ms_sum = 0.0f;
-            for (int rep = 0; rep < 2; ++rep) {  // first repetition warms up
-                BCUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), b->stream), "memset");
-                BCUDA(cudaEventRecord(e0, b->stream), "event");
-                BCUDA(harm::batch_launch(launch_desc(b, total), b->stream), "batched launch");
-                BCUDA(cudaEventRecord(e1, b->stream), "event");
-                BCUDA(cudaEventSynchronize(e1), "event");
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep == 1) ms_sum = ms;
-            }
-            if (ms_sum < best) {
-                best = ms_sum;
-                best_ty = cand[c];
-            }
+        for (int i = 0; i < (int)members.size() && i < kSampleScenes; ++i) use[members[i]] = sample_all[members[i]] = 1;
+        const TuneKey key{b->device, b->variant, b->nc, b->taps, b->share3, cls};
+        ClassChoice best{16, b->scenes[members[0]]->mixed.nb};
+        auto it = g_class_choice.find(key);
+        if (it != g_class_choice.end()) {
+            best = it->second;
+        } else {
+            float best_ms = 1e30f;
+            const int rows[2] = {16, 8};
+            const int wins[2] = {b->scenes[members[0]]->mixed.nb, b->scenes[members[0]]->mixed.alt_nb};
+            for (int r = 0; r < 2 && st == HARM_OK; ++r)
+                for (int w = 0; w < 2 && st == HARM_OK; ++w) {
+                    std::vector<int> win = b->win;
+                    for (int m : members) {
+                        b->ty[m] = rows[r];
+                        win[m] = wins[w];
+                    }
+                    float ms = 0.0f;
+                    if ((st = set_windows(b, win)) != HARM_OK) break;
+                    if ((st = time_sample(b, kSamplePulses, use, kReps, e0, e1, &ms)) != HARM_OK) break;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = ClassChoice{rows[r], wins[w]};
+                    }
+                }
+            if (st == HARM_OK) g_class_choice[key] = best;
         }
-        if (st != HARM_OK) break;
-        for (int s = 0; s < n; ++s)
-            if (use[s]) b->ty[s] = best_ty;
+        std::vector<int> win = b->win;
+        for (int m : members) {
+            b->ty[m] = best.ty;
+            win[m] = best.win;
+        }
+        if (st == HARM_OK) st = set_windows(b, win);
+    }
+    // CTAs per SM of the launch, timed on the samples of every class together
+    if (st == HARM_OK) {
+        const TuneKey key{b->device, b->variant, b->nc, b->taps, b->share3, 8 + class_mask};
+        auto it = g_ctas_choice.find(key);
+        if (it != g_ctas_choice.end()) {
+            b->ctas_per_sm = it->second;
+        } else {
+            const int most = (b->variant & 1) ? 1 : 2;  // the Choppy Wave Model's registers allow one CTA per SM
+            float best_ms = 1e30f;
+            int best_c = most;
+            for (int c = most; c >= 1 && st == HARM_OK; --c) {
+                b->ctas_per_sm = c;
+                float ms = 0.0f;
+                if ((st = time_sample(b, kSamplePulses, sample_all, kReps, e0, e1, &ms)) != HARM_OK) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_c = c;
+                }
+            }
+            b->ctas_per_sm = best_c;
+            if (st == HARM_OK) g_ctas_choice[key] = best_c;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != HARM_OK) return st;
+    std::vector<char> all(n, 1);
+    return plan(b, 0, all, &b->total);
+}
+
+harm_status harm_batch_config(const harm_batch *b, int32_t *rows, int32_t *windows, int32_t *ctas_per_sm)
+{
+    if (!b) return fail(HARM_E_INVALID, "batch is NULL");
+    for (size_t s = 0; s < b->scenes.size(); ++s) {
+        if (rows) rows[s] = b->ty[s];
+        if (windows) windows[s] = b->win[s];
+    }
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+    return HARM_OK;
+}
+
+harm_status harm_batch_set_config(harm_batch *b, const int32_t *rows, const int32_t *windows, int32_t ctas_per_sm)
+{
+    if (!b || !rows || !windows) return fail(HARM_E_INVALID, "NULL argument");
+    const int n = (int)b->scenes.size();
+    for (int s = 0; s < n; ++s) {
+        if (rows[s] != 8 && rows[s] != 16) return fail(HARM_E_INVALID, "tile rows of scene %d: %d (8 or 16)", s, rows[s]);
+        const harm::MixedTables &M = b->scenes[s]->mixed;
+        if (windows[s] != M.nb && windows[s] != M.alt_nb)
+            return fail(HARM_E_INVALID, "window of scene %d: %d (%d or %d pulses)", s, windows[s], M.nb, M.alt_nb);
+    }
+    const int most = (b->variant & 1) ? 1 : 2;
+    if (ctas_per_sm < 1 || ctas_per_sm > most)
+        return fail(HARM_E_INVALID, "ctas_per_sm %d (1 .. %d for this batch)", ctas_per_sm, most);
+    BCUDA(cudaStreamSynchronize(b->stream), "sync");
+    drop_graph(b);
+    for (int s = 0; s < n; ++s) b->ty[s] = rows[s];
+    std::vector<int> win(windows, windows + n);
+    harm_status st = set_windows(b, win);
+    if (st != HARM_OK) return st;
+    b->ctas_per_sm = ctas_per_sm;
     std::vector<char> all(n, 1);
     return plan(b, 0, all, &b->total);
 }

@@ -211,7 +211,7 @@ harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps,
 {
     const harm_scene_desc &d = s->desc;
     MixedTables &M = s->mixed;
-    const int nx = d.nx, ny = d.ny, np = d.n_pulses;
+    const int np = d.n_pulses;
     const int nw = W.nw, nsets = W.n_sets;
     const int nf = d.cwm ? 8 : 3;
     M.nb = mixed_batch_pulses();
@@ -230,19 +230,30 @@ harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps,
     // tc[b][set][m] = e^{-i omega t_c(b)}; cr[set][m][f][o] = the signed real factor
     // (c or g) r_o (the kernels pair orders 2p, 2p + 1 with (Q_r, Q_i) for real c_f
     // and with (Q_i, Q_r) for imaginary c_f).
-    std::vector<float> tau(np);
-    std::vector<float2> tc((size_t)M.n_batches * nsw);
+    // time tables of the windows: offsets tau from the window centre and the
+    // centre phasors, for the default window and for the half-length one
+    auto window_tables = [&](int nb, std::vector<float> &tau, std::vector<float2> &tc) {
+        const int nbat = (np + nb - 1) / nb;
+        tau.assign(np, 0.0f);
+        tc.assign((size_t)nbat * nsw, make_float2(0.0f, 0.0f));
+        for (int b = 0; b < nbat; ++b) {
+            int first = b * nb, last = std::min(np, first + nb) - 1;
+            double tcb = 0.5 * (ps[first].ts + ps[last].ts);
+            for (int n = first; n <= last; ++n) tau[n] = (float)(ps[n].ts - tcb);
+            for (int q = 0; q < nsets; ++q)
+                for (int m = 0; m < nw; ++m) {
+                    const double a = -W.at(q, m).om * tcb;
+                    tc[(size_t)b * nsw + (size_t)q * nw + m] = make_float2((float)std::cos(a), (float)std::sin(a));
+                }
+        }
+    };
+    std::vector<float> tau, tau_alt;
+    std::vector<float2> tc, tc_alt;
+    window_tables(M.nb, tau, tc);
+    M.alt_nb = M.nb / 2;
+    M.alt_n_batches = (np + M.alt_nb - 1) / M.alt_nb;
+    window_tables(M.alt_nb, tau_alt, tc_alt);
     std::vector<float> cr(nsw * nf * kOrders);
-    for (int b = 0; b < M.n_batches; ++b) {
-        int first = b * M.nb, last = std::min(np, first + M.nb) - 1;
-        double tcb = 0.5 * (ps[first].ts + ps[last].ts);
-        for (int n = first; n <= last; ++n) tau[n] = (float)(ps[n].ts - tcb);
-        for (int q = 0; q < nsets; ++q)
-            for (int m = 0; m < nw; ++m) {
-                const double a = -W.at(q, m).om * tcb;
-                tc[(size_t)b * nsw + (size_t)q * nw + m] = make_float2((float)std::cos(a), (float)std::sin(a));
-            }
-    }
     static const double kSignReal[kOrders] = {1.0, 1.0, -1.0, -1.0, 1.0, 1.0};
     static const double kSignImag[kOrders] = {-1.0, 1.0, 1.0, -1.0, -1.0, 1.0};
     for (int q = 0; q < nsets; ++q)
@@ -266,7 +277,8 @@ harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps,
     fit_sinc2(M.sinc2);
     if (phasor_tables<float2>(s, W, nullptr, &M.ex, &M.ey, nullptr) != cudaSuccess ||
         upload_raw(s, tc, &M.tc) != cudaSuccess || upload_raw(s, cr, &M.cr) != cudaSuccess ||
-        upload_raw(s, tau, &M.tau) != cudaSuccess)
+        upload_raw(s, tau, &M.tau) != cudaSuccess || upload_raw(s, tc_alt, &M.alt_tc) != cudaSuccess ||
+        upload_raw(s, tau_alt, &M.alt_tau) != cudaSuccess)
         return HARM_E_CUDA;
     return HARM_OK;
 }

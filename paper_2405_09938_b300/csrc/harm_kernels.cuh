@@ -25,6 +25,11 @@ struct MixedTables {
     const float2 *tc = nullptr;   // [n_batches][n_sets][nw] e^{-i omega t_c} at the batch centre
     const float *cr = nullptr;    // [n_sets][nw][nf][kOrders] signed real Taylor coefficients
     const float *tau = nullptr;   // [np_total] t_s(n) - t_centre(batch)
+    // the same time tables for windows of half the length (alt_nb pulses), which the
+    // batched launch's autotuner may pick per scene-size class
+    int alt_nb = 0, alt_n_batches = 0;
+    const float2 *alt_tc = nullptr;  // [alt_n_batches][n_sets][nw]
+    const float *alt_tau = nullptr;  // [np_total]
     float tap[8][kTapDeg + 1];    // Kaiser-sinc tap h(j - f), j = -3..4, monomials in t
     float sinc2[kSincDeg + 1];    // sinc^2(x) for |x| <= 1, monomials in t = 2 x^2 - 1
 };
@@ -115,7 +120,10 @@ struct BatchLaunch {
     int share3;              // every scene: 6 channels, two receive antennas of 3 phase centres
 };
 size_t batch_args_bytes();
-void batch_fill_args(const harm_scene *s, void *dst);
+// Launch arguments of a scene for a batched launch whose work items span `window`
+// pulses (the scene's time-Taylor window, or the half-length alternative).
+void batch_fill_args(const harm_scene *s, void *dst, int window);
+int batch_windows(const harm_scene *s, int window);  // work items along the burst for that window
 int batch_tiles(const harm_scene *s, int ty);
 int batch_variant(const harm_scene *s);  // surface model / pattern kind of the per-pulse code
 bool batch_share3(const harm_scene *s);  // 6 channels in two antennas of 3 phase centres

@@ -107,7 +107,7 @@ extern "C" harm_status harm_batch_run_noalloc(harm_scene *const *scenes, int32_t
     double cost[kMaxScenes];
     for (int s = 0; s < n; ++s) {
         const harm_scene *sc = scenes[s];
-        harm::batch_fill_args(sc, h.args + (size_t)s * ab);  // the kernel strides by the block size
+        harm::batch_fill_args(sc, h.args + (size_t)s * ab, sc->mixed.nb);  // the kernel strides by the block size
         h.ty[s] = 16;
         h.tiles[s] = harm::batch_tiles(sc, 16);
         h.iq[s] = (float *)iq_dev[s];

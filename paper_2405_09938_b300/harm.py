@@ -91,6 +91,8 @@ SIGNATURES = {
     "harm_batch_tune": (C.c_int, [_VP, C.POINTER(_VP)]),
     "harm_batch_tile_rows": (C.c_int, [_VP, C.POINTER(C.c_int32)]),
     "harm_batch_set_tile_rows": (C.c_int, [_VP, C.POINTER(C.c_int32)]),
+    "harm_batch_config": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "harm_batch_set_config": (C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32]),
     "harm_batch_run": (C.c_int, [_VP, C.POINTER(_VP), C.c_int32]),
     "harm_batch_destroy": (C.c_int, [_VP]),
     "harm_batch_run_noalloc": (C.c_int, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP), C.c_int32]),
@@ -451,8 +453,10 @@ def harm_batch_create(scenes) -> Batch:
 
 
 def harm_batch_tune(batch: Batch, iqs):
-    """Time 8- and 16-row tiles per scene-size class and keep the faster;
-    overwrites the complex64 CUDA tensors `iqs` (one per scene). Synchronous."""
+    """Pick the launch shape (tile rows and time-Taylor window per scene-size
+    class, CTAs per SM) by timing, or from the choices already made in this
+    process for batches of the same kind; overwrites the complex64 CUDA tensors
+    `iqs` (one per scene). Synchronous."""
     _check(load_library().harm_batch_tune(batch.handle, _ptr_array(iqs, "iq", batch.scenes)))
 
 
@@ -467,6 +471,23 @@ def harm_batch_set_tile_rows(batch: Batch, rows):
     """Pin the tile height (8 or 16) of each scene instead of tuning."""
     arr = (C.c_int32 * len(batch.scenes))(*[int(r) for r in rows])
     _check(load_library().harm_batch_set_tile_rows(batch.handle, arr))
+
+
+def harm_batch_config(batch: Batch):
+    """Launch shape in use: {"rows": [...], "windows": [...], "ctas_per_sm": c}."""
+    n = len(batch.scenes)
+    rows, wins, cps = (C.c_int32 * n)(), (C.c_int32 * n)(), C.c_int32()
+    _check(load_library().harm_batch_config(batch.handle, rows, wins, C.byref(cps)))
+    return {"rows": [int(v) for v in rows], "windows": [int(v) for v in wins], "ctas_per_sm": int(cps.value)}
+
+
+def harm_batch_set_config(batch: Batch, rows, windows, ctas_per_sm: int):
+    """Pin the launch shape: rows 8 or 16 and windows (a scene's pulse_batch or
+    half of it) per scene, ctas_per_sm 1 or 2."""
+    n = len(batch.scenes)
+    r = (C.c_int32 * n)(*[int(v) for v in rows])
+    w = (C.c_int32 * n)(*[int(v) for v in windows])
+    _check(load_library().harm_batch_set_config(batch.handle, r, w, int(ctas_per_sm)))
 
 
 def harm_batch_run(batch: Batch, iqs, zero_first: bool = True):

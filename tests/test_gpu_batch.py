@@ -133,6 +133,52 @@ def test_batch_eight_row_tiles():
         s.close()
 
 
+def test_batch_config_windows_and_ctas():
+    """Half-length time-Taylor windows on some scenes and one CTA per SM: the same
+    echo as the single-scene accumulator (full windows, two CTAs per SM) within
+    the Taylor truncation of the longer window; bad shapes are refused."""
+    import time
+
+    import torch
+    descs = _uneven_scenes()
+    scenes = [harm.harm_scene_create(d, harm.HARM_PREC_MIXED) for d in descs]
+    pb = harm.harm_scene_query(scenes[0])["pulse_batch"]
+    b = harm.harm_batch_create(scenes)
+    cfg = harm.harm_batch_config(b)
+    assert cfg == {"rows": [16] * 5, "windows": [pb] * 5, "ctas_per_sm": 2}
+    for bad in (([16] * 5, [pb] * 4 + [pb // 4], 2), ([16] * 5, [pb] * 5, 3), ([16] * 5, [pb] * 5, 0),
+                ([16, 16, 16, 16, 4], [pb] * 5, 1)):
+        with pytest.raises(harm.HarmError):
+            harm.harm_batch_set_config(b, *bad)
+    harm.harm_batch_set_config(b, [16, 8, 16, 8, 16], [pb // 2, pb, pb // 2, pb // 2, pb], 1)
+    assert harm.harm_batch_config(b) == {"rows": [16, 8, 16, 8, 16], "windows": [pb // 2, pb, pb // 2, pb // 2, pb],
+                                         "ctas_per_sm": 1}
+    iqs = _batch_outputs(descs)
+    harm.harm_batch_run(b, iqs)
+    torch.cuda.synchronize()
+    for d, t in zip(descs, iqs):
+        assert_iq(t.cpu().numpy(), _single(d), 1e-5)
+    # the tuner's choices are kept for the process: a second batch of the same kind
+    # is configured without timing, to the same shape
+    harm.harm_batch_tune(b, iqs)
+    first = harm.harm_batch_config(b)
+    b2 = harm.harm_batch_create(scenes)
+    t0 = time.perf_counter()
+    harm.harm_batch_tune(b2, iqs)
+    dt = time.perf_counter() - t0
+    assert harm.harm_batch_config(b2) == first
+    print("tuned shape:", first, "second tune %.3f s" % dt)
+    assert dt < 0.5
+    harm.harm_batch_run(b2, iqs)
+    torch.cuda.synchronize()
+    for d, t in zip(descs, iqs):
+        assert_iq(t.cpu().numpy(), _single(d), 1e-5)
+    b.close()
+    b2.close()
+    for s in scenes:
+        s.close()
+
+
 def test_batch_rejects_bad_inputs():
     descs = _uneven_scenes()[:2]
     s64 = harm.harm_scene_create(descs[0], harm.HARM_PREC_FP64)
