@@ -710,14 +710,15 @@ def measure_batched(args, stream):
 
 def measure_generator(args, stream, flush):
     """The facet generator on its own (harm_facets_generate): states (eta, eta_x,
-    eta_y) of every facet of the headline scene for one 128-pulse window, written
-    to HBM as float32 [128][3][n_facets] (3.07 GB); one warm-up, then the mean of
-    three timed runs, L2 flushed before each. Bound by the HBM write stream."""
+    eta_y) of every facet of the headline scene for the first 256 pulses (one
+    time-Taylor window), written to HBM as float32 [256][3][n_facets] (6.14 GB);
+    one warm-up, then the mean of three timed runs, L2 flushed before each. Bound
+    by the HBM write stream."""
     import torch
     from paper_2405_09938_b300 import harm
     d = hs.ati_scene()
     scene = harm.harm_scene_create(d, harm.HARM_PREC_MIXED, stream)
-    npw = 128
+    npw = harm.harm_scene_query(scene)["pulse_batch"]
     st = torch.empty((npw, 3, d["ny"], d["nx"]), dtype=torch.float32, device="cuda")
     times = []
     for i in range(4):
@@ -738,7 +739,7 @@ def measure_generator(args, stream, flush):
     peaks = measured_peaks() or {}
     hbm = peaks.get("hbm_gbs")
     gbs = nbytes / (ms * 1e-3) / 1e9
-    return {"workload": "ati_4x2km_states_128p", "facet_pulses": hs.n_facets(d) * npw, "ms": ms,
+    return {"workload": "ati_4x2km_states_%dp" % npw, "facet_pulses": hs.n_facets(d) * npw, "ms": ms,
             "value": hs.n_facets(d) * npw / (ms * 1e-3), "unit": "facet-pulse states/s",
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                          "frac": gbs / hbm if hbm else None,

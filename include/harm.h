@@ -193,10 +193,25 @@ harm_status harm_facets_generate(harm_scene *scene, int32_t n0, int32_t np, void
 /* Echo accumulator (Eq. 3, 4, 16, 17): adds the echo of every facet for pulses
    [n0, n0 + np) and every channel into iq_dev, laid out [n_channels][np][n_range]
    complex of `dtype`. zero_first = 1 clears iq_dev first (on the stream).
-   Sums use atomics: repeated runs agree to rounding, not bit for bit.
-   Errors: HARM_E_INVALID (window, pointer, dtype). */
+   Sums use floating-point atomics: repeated runs agree to rounding, not bit for
+   bit, unless the scene is in deterministic mode (harm_scene_set_deterministic).
+   Errors: HARM_E_INVALID (window, pointer, dtype), HARM_E_UNSUPPORTED (a
+   complex64 output in deterministic mode). */
 harm_status harm_echo_accumulate(harm_scene *scene, int32_t n0, int32_t np, void *iq_dev,
                                  harm_dtype dtype, int32_t zero_first);
+
+/* Deterministic mode of a plain-path scene (HARM_PREC_FP64 or HARM_PREC_FP32;
+   on = 0 turns it off): harm_echo_accumulate and harm_echo_accumulate_host then
+   round every contribution to a multiple of 2^-40 and add it as a 64-bit integer,
+   so that the sums are exact and repeated runs give bit-identical IQ whatever
+   order the atomic additions take (the output must be complex128; the buffer
+   holds the fixed-point values during the call and FP64 again when it ends).
+   Range: every real and imaginary IQ part, including values already in the
+   buffer when zero_first = 0, below 2^23 in magnitude (larger values already
+   present are clamped and reported by harm_scene_sync as a bounds error). The
+   rounding adds at most 2^-41 per contribution. Errors: HARM_E_INVALID (NULL),
+   HARM_E_UNSUPPORTED (a mixed-precision scene). */
+harm_status harm_scene_set_deterministic(harm_scene *scene, int32_t on);
 
 /* Echo into HOST memory (Sec. IV-B: raw data leave the GPU while the next part
    is computed): writes the IQ of pulses [n0, n0 + np) to iq_host, laid out

@@ -20,6 +20,8 @@
 // the IQ with one atomic per bin and channel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "harm_internal.cuh"
 #include "harm_kernels.cuh"
 #include "philox.cuh"
@@ -237,6 +239,45 @@ __device__ __forceinline__ void global_add(OutT *iq, size_t idx, R re, R im)
     atomicAdd(iq + 2 * idx + 1, (OutT)im);
 }
 
+// Deterministic sums: every contribution is rounded to a multiple of 2^-40 and
+// added as a 64-bit integer (two's complement), so that the sum is exact and does
+// not depend on the order of the atomic additions (reproducible summation by
+// fixed-point accumulation). Range: |sum| < 2^23 per component.
+constexpr double kFixedScale = 1099511627776.0;  // 2^40
+constexpr double kFixedLimit = 8388608.0;        // 2^23
+
+__device__ __forceinline__ unsigned long long to_fixed(double v)
+{
+    return (unsigned long long)__double2ll_rn(v * kFixedScale);
+}
+
+__device__ __forceinline__ void fixed_add(unsigned long long *p, double re, double im)
+{
+    atomicAdd(p, to_fixed(re));
+    atomicAdd(p + 1, to_fixed(im));
+}
+
+// In-place conversions of an IQ buffer of n doubles between FP64 and the fixed
+// point of the deterministic sums (values outside the range are clamped and
+// counted in flags[1]).
+__global__ void fixed_from_double_kernel(double *v, size_t n, unsigned int *flags)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double x = v[i];
+        if (!(fabs(x) < kFixedLimit)) {
+            atomicAdd(flags + 1, 1u);
+            x = x > 0.0 ? kFixedLimit : (x < 0.0 ? -kFixedLimit : 0.0);
+        }
+        reinterpret_cast<unsigned long long *>(v)[i] = to_fixed(x);
+    }
+}
+
+__global__ void double_from_fixed_kernel(double *v, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        v[i] = (double)reinterpret_cast<const long long *>(v)[i] * (1.0 / kFixedScale);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) generate_plain_kernel(DevScene S, int n0, int nfirst, R *state)
 {
@@ -263,12 +304,19 @@ struct PlainProbe {
     int *cells;                // [nf]
 };
 
-template <typename R, int TAPS, typename OutT, bool PROBE>
+// DET: deterministic fixed-point sums (see to_fixed; OutT double, the IQ buffer
+// holding fixed-point values during the launch).
+template <typename R, int TAPS, typename OutT, bool PROBE, bool DET>
 __global__ void __launch_bounds__(256)
     accumulate_plain_kernel(DevScene S, int n0, int np, int nfirst, OutT *iq, PlainProbe<R> probe)
 {
     using R2 = typename M<R>::R2;
-    __shared__ R2 tile[kMaxCh][kWin];
+    static_assert(!DET || sizeof(OutT) == 8, "deterministic sums need complex128 output");
+    // range tile of the CTA: R2 values, or (re, im) fixed-point pairs
+    __shared__ __align__(16) unsigned char tile_raw[kMaxCh * kWin * (DET ? 16 : sizeof(R2))];
+    R2(*tile)[kWin] = reinterpret_cast<R2(*)[kWin]>(tile_raw);
+    unsigned long long(*tileq)[kWin][2] = reinterpret_cast<unsigned long long(*)[kWin][2]>(tile_raw);
+    unsigned long long *iqq = reinterpret_cast<unsigned long long *>(iq);
     __shared__ int kbase[kMaxCh];
 
     const int tiles_x = (S.nx + kTile - 1) / kTile;
@@ -281,7 +329,14 @@ __global__ void __launch_bounds__(256)
     const int nr = S.nr;
     const PulseState &P = S.pulses[n];
 
-    for (int i = threadIdx.x; i < S.nc * kWin; i += blockDim.x) tile[i / kWin][i % kWin] = M<R>::pair(R(0), R(0));
+    for (int i = threadIdx.x; i < S.nc * kWin; i += blockDim.x) {
+        if constexpr (DET) {
+            tileq[i / kWin][i % kWin][0] = 0ull;
+            tileq[i / kWin][i % kWin][1] = 0ull;
+        } else {
+            tile[i / kWin][i % kWin] = M<R>::pair(R(0), R(0));
+        }
+    }
     // Window base per channel from the tile centre on the mean surface (FP64: a
     // per-tile value that only places the shared-memory window).
     if (threadIdx.x < S.nc) {
@@ -396,7 +451,11 @@ __global__ void __launch_bounds__(256)
                 if (fk >= R(0) && fk < (R)nr) {
                     const int k = (int)fk;
                     const int w = k - kbase[c];
-                    if (w >= 0 && w < kWin) {
+                    if (DET && w >= 0 && w < kWin) {
+                        fixed_add(tileq[c][w], (double)vr, (double)vi);
+                    } else if (DET) {
+                        fixed_add(iqq + 2 * (((size_t)c * np + (n - n0)) * nr + k), (double)vr, (double)vi);
+                    } else if (w >= 0 && w < kWin) {
                         atomicAdd(&tile[c][w].x, vr);
                         atomicAdd(&tile[c][w].y, vi);
                     } else {
@@ -414,7 +473,12 @@ __global__ void __launch_bounds__(256)
                     if (k < 0 || k >= nr) continue;
                     const R h = kaiser_sinc<R>(S, (R)j - fr, spf, j);
                     const int w = k - kbase[c];
-                    if (w >= 0 && w < kWin) {
+                    if (DET && w >= 0 && w < kWin) {
+                        fixed_add(tileq[c][w], (double)(h * vr), (double)(h * vi));
+                    } else if (DET) {
+                        fixed_add(iqq + 2 * (((size_t)c * np + (n - n0)) * nr + k), (double)(h * vr),
+                                  (double)(h * vi));
+                    } else if (w >= 0 && w < kWin) {
                         atomicAdd(&tile[c][w].x, h * vr);
                         atomicAdd(&tile[c][w].y, h * vi);
                     } else {
@@ -429,9 +493,16 @@ __global__ void __launch_bounds__(256)
     for (int i = threadIdx.x; i < S.nc * kWin; i += blockDim.x) {
         const int c = i / kWin, w = i % kWin;
         const int k = kbase[c] + w;
-        const R2 v = tile[c][w];
-        if (k >= 0 && k < nr && (v.x != R(0) || v.y != R(0)))
-            global_add<OutT, R>(iq, ((size_t)c * np + (n - n0)) * nr + k, v.x, v.y);
+        if (k < 0 || k >= nr) continue;
+        if constexpr (DET) {
+            const unsigned long long re = tileq[c][w][0], im = tileq[c][w][1];
+            unsigned long long *o = iqq + 2 * (((size_t)c * np + (n - n0)) * nr + k);
+            if (re) atomicAdd(o, re);
+            if (im) atomicAdd(o + 1, im);
+        } else {
+            const R2 v = tile[c][w];
+            if (v.x != R(0) || v.y != R(0)) global_add<OutT, R>(iq, ((size_t)c * np + (n - n0)) * nr + k, v.x, v.y);
+        }
     }
 }
 
@@ -449,24 +520,47 @@ cudaError_t generate_r(const DevScene &S, cudaStream_t st, int n0, int np, R *st
     return cudaSuccess;
 }
 
-template <typename R, int TAPS, typename OutT, bool PROBE>
+template <typename R, int TAPS, typename OutT, bool PROBE, bool DET = false>
 cudaError_t accumulate_r(const DevScene &S, cudaStream_t st, int n0, int np, OutT *iq, const PlainProbe<R> &probe)
 {
     const int tiles = ((S.nx + kTile - 1) / kTile) * ((S.ny + kTile - 1) / kTile);
     for (int p0 = 0; p0 < np; p0 += 65535) {
         const int cnt = min(65535, np - p0);
         dim3 grid((unsigned)tiles, (unsigned)cnt);
-        accumulate_plain_kernel<R, TAPS, OutT, PROBE><<<grid, 256, 0, st>>>(S, n0, np, n0 + p0, iq, probe);
+        accumulate_plain_kernel<R, TAPS, OutT, PROBE, DET><<<grid, 256, 0, st>>>(S, n0, np, n0 + p0, iq, probe);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
+// Deterministic sums into a complex128 IQ: the buffer is converted to fixed point
+// in place (so that it may already hold values to add to), accumulated with
+// integer atomics, and converted back.
+template <typename R>
+cudaError_t accumulate_det(const DevScene &S, cudaStream_t st, int n0, int np, double *iq)
+{
+    const size_t n = (size_t)2 * S.nc * np * S.nr;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 148 * 8);
+    fixed_from_double_kernel<<<blocks, 256, 0, st>>>(iq, n, S.flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const PlainProbe<R> none{};
+    e = S.taps == 1 ? accumulate_r<R, 1, double, false, true>(S, st, n0, np, iq, none)
+                    : accumulate_r<R, 8, double, false, true>(S, st, n0, np, iq, none);
+    if (e != cudaSuccess) return e;
+    double_from_fixed_kernel<<<blocks, 256, 0, st>>>(iq, n);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t accumulate_dtype(const DevScene &S, cudaStream_t st, int n0, int np, void *iq, harm_dtype dtype)
 {
     const PlainProbe<R> none{};
+    if (S.det) {
+        if (dtype != HARM_C128) return cudaErrorNotSupported;
+        return accumulate_det<R>(S, st, n0, np, (double *)iq);
+    }
     if (dtype == HARM_C128)
         return S.taps == 1 ? accumulate_r<R, 1, double, false>(S, st, n0, np, (double *)iq, none)
                            : accumulate_r<R, 8, double, false>(S, st, n0, np, (double *)iq, none);

@@ -151,6 +151,8 @@ extern "C" harm_status harm_echo_accumulate_host(harm_scene *s, int32_t n0, int3
     if (np < 0 || n0 < 0 || (int64_t)n0 + np > s->desc.n_pulses)
         return fail(HARM_E_INVALID, "pulse window [%d, %d) outside [0, %d)", n0, n0 + np, s->desc.n_pulses);
     if (dtype != HARM_C64 && dtype != HARM_C128) return fail(HARM_E_INVALID, "unknown dtype %d", (int)dtype);
+    if (s->dev.det && dtype != HARM_C128)
+        return fail(HARM_E_UNSUPPORTED, "deterministic sums need complex128 output");
     int dev = -1;
     HCUDA(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev != s->device) return fail(HARM_E_INVALID, "scene lives on device %d, current device is %d", s->device, dev);

@@ -80,6 +80,7 @@ struct DevScene {
     unsigned int lut_mask;      // bit 0: transmitter grid, bit 1 + c: receive channel c grid
     const PatLut *luts;         // [1 + nc] (device)
     const double *kn;           // [n_sets][nw] |k| (CWM direction cosines of the waves)
+    int det;                    // plain paths: deterministic fixed-point sums (complex128 output)
     unsigned int rx_share;      // bit c: channel c is a phase centre of channel c - 1's receive
                                 // antenna (mixed path: the analytic pattern gain is shared)
 };

@@ -9,6 +9,7 @@
 // work list, output pointer table and the work counter) in one file-scope device
 // array of fixed size instead of buffers from cudaMalloc. Scenes and outputs are
 // still passed in by the caller.
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 
@@ -26,15 +27,17 @@ constexpr int kMaxScenes = 64;       // scenes per call
 constexpr int kArgsBytes = 2048;     // bytes reserved per scene argument block
 constexpr int kMaxDevices = 64;
 
-// Layout of the scratch image (host copy uploaded in one transfer per call).
+// Layout of the scratch image (host copy uploaded in one transfer per call): the
+// small tables first and the per-scene argument blocks last, so that a call
+// uploads only the tables and the blocks of its own scenes.
 struct ScratchImage {
-    unsigned char args[kMaxScenes * kArgsBytes];
     int start[kMaxScenes + 1];
     int tiles[kMaxScenes];
     int ty[kMaxScenes];
     int order[kMaxScenes];
     float *iq[kMaxScenes];
     unsigned int counter;
+    alignas(16) unsigned char args[kMaxScenes * kArgsBytes];
 };
 
 // The scratch memory: every GPU that loads the library holds one copy until the
@@ -130,7 +133,8 @@ extern "C" harm_status harm_batch_run_noalloc(harm_scene *const *scenes, int32_t
     h.counter = 0u;  // the work counter must start at zero on every call
 
     cudaStream_t stream = scenes[0]->stream;
-    cudaError_t e = cudaMemcpyAsync(base, &h, sizeof(ScratchImage), cudaMemcpyHostToDevice, stream);
+    const size_t used = offsetof(ScratchImage, args) + (size_t)n * ab;
+    cudaError_t e = cudaMemcpyAsync(base, &h, used, cudaMemcpyHostToDevice, stream);
     for (int s = 0; e == cudaSuccess && zero_first && s < n; ++s) {
         const harm_scene *sc = scenes[s];
         e = cudaMemsetAsync(iq_dev[s], 0, (size_t)sc->desc.n_channels * sc->desc.n_pulses * sc->desc.n_range * 8,

@@ -572,6 +572,15 @@ harm_status harm_facets_generate(harm_scene *s, int32_t n0, int32_t np, void *st
     return HARM_OK;
 }
 
+harm_status harm_scene_set_deterministic(harm_scene *s, int32_t on)
+{
+    if (!s) return fail(HARM_E_INVALID, "scene is NULL");
+    if (on && s->desc.precision == HARM_PREC_MIXED)
+        return fail(HARM_E_UNSUPPORTED, "deterministic sums are offered by the plain paths (FP64, FP32)");
+    s->dev.det = on ? 1 : 0;
+    return HARM_OK;
+}
+
 harm_status harm_echo_accumulate(harm_scene *s, int32_t n0, int32_t np, void *iq_dev, harm_dtype dtype,
                                  int32_t zero_first)
 {
@@ -579,6 +588,8 @@ harm_status harm_echo_accumulate(harm_scene *s, int32_t n0, int32_t np, void *iq
     if (st != HARM_OK) return st;
     if ((st = check_device(s)) != HARM_OK) return st;
     if (dtype != HARM_C64 && dtype != HARM_C128) return fail(HARM_E_INVALID, "unknown dtype %d", (int)dtype);
+    if (s->dev.det && dtype != HARM_C128)
+        return fail(HARM_E_UNSUPPORTED, "deterministic sums need complex128 output");
     if (np == 0) return HARM_OK;
     size_t bytes = (size_t)s->desc.n_channels * np * s->desc.n_range * (dtype == HARM_C64 ? 8 : 16);
     if ((st = check_ptr(iq_dev, bytes, "iq_dev")) != HARM_OK) return st;

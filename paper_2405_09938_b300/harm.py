@@ -97,6 +97,7 @@ SIGNATURES = {
     "harm_batch_destroy": (C.c_int, [_VP]),
     "harm_batch_run_noalloc": (C.c_int, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP), C.c_int32]),
     "harm_probe_indices": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP, _VP, _VP, _VP]),
+    "harm_scene_set_deterministic": (C.c_int, [_VP, C.c_int32]),
     "harm_last_error": (C.c_char_p, []),
 }
 
@@ -345,6 +346,12 @@ def harm_echo_accumulate(scene: Scene, n0: int, np_: int, iq, zero_first: bool =
     ptr = _dev_ptr(iq, "iq", (scene, _iq_numel(scene, np_)))
     _check(load_library().harm_echo_accumulate(scene.handle, n0, np_, ptr, _dtype_code(iq),
                                                1 if zero_first else 0))
+
+
+def harm_scene_set_deterministic(scene: Scene, on: bool = True):
+    """Deterministic (bit-reproducible) fixed-point sums for a plain-path scene
+    (FP64 or FP32); needs complex128 IQ outputs."""
+    _check(load_library().harm_scene_set_deterministic(scene.handle, 1 if on else 0))
 
 
 def harm_echo_accumulate_host(scene: Scene, n0: int, np_: int, iq_host, block_pulses: int = 0):

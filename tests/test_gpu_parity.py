@@ -258,3 +258,61 @@ def test_repeat_runs_agree():
     a = run_echo(d, harm.HARM_PREC_MIXED, 0, 32, "c64")
     b = run_echo(d, harm.HARM_PREC_MIXED, 0, 32, "c64")
     assert_iq(a, b, 1e-6)
+
+
+# ------------------------------------------------------------------ deterministic sums
+def _det_run(d, prec, n0, np_, scene=None, zero_first=True, iq=None):
+    import torch
+    sc = scene or harm.harm_scene_create(d, prec)
+    harm.harm_scene_set_deterministic(sc, True)
+    if iq is None:
+        iq = torch.zeros((len(d["rx"]), np_, d["n_range"]), dtype=torch.complex128, device="cuda")
+    harm.harm_echo_accumulate(sc, n0, np_, iq, zero_first=zero_first)
+    harm.harm_scene_sync(sc)
+    out = iq.cpu().numpy()
+    if scene is None:
+        sc.close()
+    return out, iq
+
+
+@pytest.mark.parametrize("prec", [harm.HARM_PREC_FP64, harm.HARM_PREC_FP32])
+def test_deterministic_sums_are_bit_identical(prec):
+    """Fixed-point (integer-atomic) sums of the plain paths: two runs give the same
+    bits, the second of two accumulating runs is exactly twice the first, and the
+    result keeps the path's accuracy against the oracle. This is the run-to-run
+    race check of the accumulator (floating-point atomics agree only to rounding)."""
+    import torch
+    d = small_wave_scene(n_pulses=48, nx=45, ny=37)
+    want = oracle.echo(d, list(range(5, 37)))
+    sc = harm.harm_scene_create(d, prec)
+    a, _ = _det_run(d, prec, 5, 32, scene=sc)
+    b, iq = _det_run(d, prec, 5, 32, scene=sc)
+    assert a.tobytes() == b.tobytes()
+    c, _ = _det_run(d, prec, 5, 32, scene=sc, zero_first=False, iq=iq)
+    assert c.tobytes() == (2 * a).tobytes()
+    tol = TOL_FP64 if prec == harm.HARM_PREC_FP64 else 1e-3
+    assert_iq(a, want, tol)
+    # the floating-point atomics of the default mode: same result to rounding
+    harm.harm_scene_set_deterministic(sc, False)
+    f = run_echo(d, prec, 5, 32, "c128", scene=sc)
+    assert rel_rms(f, a) < (1e-12 if prec == harm.HARM_PREC_FP64 else 1e-6)
+    # complex64 output cannot hold the fixed-point sums
+    harm.harm_scene_set_deterministic(sc, True)
+    with pytest.raises(harm.HarmError) as e:
+        harm.harm_echo_accumulate(sc, 5, 32, torch.zeros((6, 32, d["n_range"]), dtype=torch.complex64, device="cuda"))
+    assert e.value.status == harm.HARM_E_UNSUPPORTED
+    # the host-output path runs the same deterministic accumulator per block
+    host = torch.zeros((6, 32, d["n_range"]), dtype=torch.complex128, pin_memory=True)
+    harm.harm_echo_accumulate_host(sc, 5, 32, host, block_pulses=12)
+    harm.harm_scene_sync(sc)
+    assert host.numpy().tobytes() == a.tobytes()
+    sc.close()
+
+
+def test_deterministic_mode_refused_for_mixed_scene():
+    sc = harm.harm_scene_create(small_wave_scene(n_pulses=8, nx=16, ny=16), harm.HARM_PREC_MIXED)
+    with pytest.raises(harm.HarmError) as e:
+        harm.harm_scene_set_deterministic(sc, True)
+    assert e.value.status == harm.HARM_E_UNSUPPORTED
+    harm.harm_scene_set_deterministic(sc, False)
+    sc.close()

@@ -46,6 +46,41 @@ def test_noalloc_matches_batch_run_twice():
         s.close()
 
 
+def test_noalloc_64_scenes_and_accumulation():
+    """The largest call (64 scenes: every argument slot and the ends of the work
+    tables in the fixed array) against harm_batch_run, then a call with
+    zero_first = 0 into prefilled outputs: prefill + echo."""
+    import numpy as np
+    import torch
+    descs = []
+    for i in range(64):
+        d = hs.ati_scene(n_pulses=12 + (i % 5) * 4, nx=20 + (i % 7) * 6, ny=17 + (i % 3) * 9, n_range=256)
+        d["speckle_seed"], d["u10"] = 500 + i, 4.0 + 0.15 * i
+        descs.append(d)
+    scenes = [harm.harm_scene_create(d, harm.HARM_PREC_MIXED) for d in descs]
+    shapes = [(len(d["rx"]), d["n_pulses"], d["n_range"]) for d in descs]
+    ref = [torch.zeros(s, dtype=torch.complex64, device="cuda") for s in shapes]
+    b = harm.harm_batch_create(scenes)
+    harm.harm_batch_run(b, ref)
+    torch.cuda.synchronize()
+    want = [t.cpu().numpy() for t in ref]
+    b.close()
+    out = [torch.full(s, 2.0, dtype=torch.complex64, device="cuda") for s in shapes]
+    harm.harm_batch_run_noalloc(scenes, out, zero_first=True)
+    torch.cuda.synchronize()
+    for w, t in zip(want, out):
+        assert_iq(t.cpu().numpy(), w, TOL)
+    rng = np.random.default_rng(9)
+    pre = [(rng.standard_normal(s) + 1j * rng.standard_normal(s)).astype(np.complex64) for s in shapes]
+    out = [torch.tensor(p, device="cuda") for p in pre]
+    harm.harm_batch_run_noalloc(scenes, out, zero_first=False)
+    torch.cuda.synchronize()
+    for w, p, t in zip(want, pre, out):
+        assert_iq(t.cpu().numpy(), p + w, TOL)
+    for s in scenes:
+        s.close()
+
+
 def test_noalloc_rejects_more_than_64_scenes():
     import torch
     d = _scenes()[0]
