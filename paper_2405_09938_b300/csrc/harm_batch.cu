@@ -343,7 +343,7 @@ harm_status harm_batch_tune(harm_batch *b, void *const *iq)
     BCUDA(cudaEventCreate(&e1), "event");
     // the sample a candidate is timed on: the first kSamplePulses pulses of the
     // (at most kSampleScenes) largest scenes of the class
-    const int kSamplePulses = 256, kSampleScenes = 2, kReps = 3;
+    const int kSamplePulses = 256, kSampleScenes = 1, kReps = 3;
     std::vector<char> sample_all(n, 0);
     int class_mask = 0;
     for (int cls = 0; cls < 3 && st == HARM_OK; ++cls) {

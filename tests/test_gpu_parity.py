@@ -292,10 +292,12 @@ def test_deterministic_sums_are_bit_identical(prec):
     assert c.tobytes() == (2 * a).tobytes()
     tol = TOL_FP64 if prec == harm.HARM_PREC_FP64 else 1e-3
     assert_iq(a, want, tol)
-    # the floating-point atomics of the default mode: same result to rounding
+    # the floating-point atomics of the default mode: same result to rounding (the
+    # fixed point rounds each of the ~700 contributions of a bin by up to 2^-41,
+    # ~1e-11 of the bin's magnitude after the random walk; measured 5.2e-12)
     harm.harm_scene_set_deterministic(sc, False)
     f = run_echo(d, prec, 5, 32, "c128", scene=sc)
-    assert rel_rms(f, a) < (1e-12 if prec == harm.HARM_PREC_FP64 else 1e-6)
+    assert rel_rms(f, a) < (1e-10 if prec == harm.HARM_PREC_FP64 else 1e-6)
     # complex64 output cannot hold the fixed-point sums
     harm.harm_scene_set_deterministic(sc, True)
     with pytest.raises(harm.HarmError) as e:
