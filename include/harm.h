@@ -266,8 +266,10 @@ harm_status harm_batch_create(harm_scene *const *scenes, int32_t n_scenes, harm_
    of the class's largest scene with each tile height (16 or 8 facet rows)
    and each time-Taylor window (harm_scene_info.pulse_batch pulses per work item,
    or half of it) -- 1 untimed and 3 timed launches per candidate, median -- and
-   keeps the fastest; then it times the launch over all classes' samples with 2
-   and 1 CTAs per SM (1 only for the Choppy Wave Model) and keeps the faster. The
+   keeps the fastest, where a candidate replaces the default shape (16 rows, full
+   window, timed first) only when it is more than 2 % faster; then it times the
+   launch over all classes' samples with 2 and 1 CTAs per SM (1 only for the
+   Choppy Wave Model) and keeps the faster under the same rule. The
    choices are remembered for the life of the process per (device, surface model
    and pattern kind, channel count, taps, channel layout, size class), so a later
    batch of the same kind is configured without timing. The tile width (32

@@ -344,6 +344,10 @@ harm_status harm_batch_tune(harm_batch *b, void *const *iq)
     // the sample a candidate is timed on: the first kSamplePulses pulses of the
     // (at most kSampleScenes) largest scenes of the class
     const int kSamplePulses = 256, kSampleScenes = 1, kReps = 3;
+    // a candidate replaces the default shape (timed first) only when it is faster by
+    // more than this margin: smaller differences on the sample are within its
+    // run-to-run spread and do not carry over to the whole batch
+    const float kMargin = 0.98f;
     std::vector<char> sample_all(n, 0);
     int class_mask = 0;
     for (int cls = 0; cls < 3 && st == HARM_OK; ++cls) {
@@ -365,6 +369,7 @@ harm_status harm_batch_tune(harm_batch *b, void *const *iq)
             const int wins[2] = {b->scenes[members[0]]->mixed.nb, b->scenes[members[0]]->mixed.alt_nb};
             for (int r = 0; r < 2 && st == HARM_OK; ++r)
                 for (int w = 0; w < 2 && st == HARM_OK; ++w) {
+                    const bool is_default = r == 0 && w == 0;
                     std::vector<int> win = b->win;
                     for (int m : members) {
                         b->ty[m] = rows[r];
@@ -373,7 +378,7 @@ harm_status harm_batch_tune(harm_batch *b, void *const *iq)
                     float ms = 0.0f;
                     if ((st = set_windows(b, win)) != HARM_OK) break;
                     if ((st = time_sample(b, kSamplePulses, use, kReps, e0, e1, &ms)) != HARM_OK) break;
-                    if (ms < best_ms) {
+                    if (is_default || ms < kMargin * best_ms) {
                         best_ms = ms;
                         best = ClassChoice{rows[r], wins[w]};
                     }
@@ -401,7 +406,7 @@ harm_status harm_batch_tune(harm_batch *b, void *const *iq)
                 b->ctas_per_sm = c;
                 float ms = 0.0f;
                 if ((st = time_sample(b, kSamplePulses, sample_all, kReps, e0, e1, &ms)) != HARM_OK) break;
-                if (ms < best_ms) {
+                if (c == most || ms < kMargin * best_ms) {
                     best_ms = ms;
                     best_c = c;
                 }
