@@ -1124,13 +1124,26 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
     const AntRec2 *RX = sm.rx2 + pi * nc;
     const ChanRec2 *CH = sm.ch2 + pi * nc;
     float2 gr_prev = make_float2(0.0f, 0.0f), amps_prev = make_float2(0.0f, 0.0f);
+    // with the six-channel layout known at compile time, channels 1, 2 and 4, 5 are
+    // the second and third phase centres of the antenna of channels 0 and 3 (5 m
+    // apart): they take that channel's second-order range term, R / r and product
+    // of the common amplitude factors. Between phase centres the facet's direction
+    // changes by ~separation / R ~ 6e-6 rad, which moves the second-order term by
+    // ~1e-8 m (1.5e-6 rad of phase) and R / r by ~3e-10.
+    float2 qr_prev = make_float2(0.0f, 0.0f), rho_prev = make_float2(0.0f, 0.0f);
+    float2 ampc_prev = make_float2(0.0f, 0.0f);
 #pragma unroll CU
     for (int ch = 0; ch < nc; ++ch) {
+        const bool pc = SH3 && (ch % 3 != 0);  // a later phase centre of the antenna (compile time)
         const AntRec2 R = RX[ch];
         const ChanRec2 Q = CH[ch];
         const float2 ar = fma2(R.ux, X0, fma2(R.uy, X1, mul2(R.uz, eta)));
-        const float2 sr_ = fma2(neg2(ar), ar, b2);
-        const float2 qr = mul2(sr_, fma2(neg2(ar), R.inv2R2, R.inv2R));
+        float2 qr = qr_prev;
+        if (!pc) {
+            const float2 sr_ = fma2(neg2(ar), ar, b2);
+            qr = mul2(sr_, fma2(neg2(ar), R.inv2R2, R.inv2R));
+        }
+        qr_prev = qr;
         const float2 dr = add2(ar, qr);
         // range bins first: the warp window of the reduction is planned here, its
         // warp-wide reductions overlapping the pattern, NRCS and phase arithmetic
@@ -1140,8 +1153,12 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
         const int kba = Q.kbase + (int)kf.x - (TAPS == 1 ? 0 : 3);
         const int kbb = Q.kbase + (int)kf.y - (TAPS == 1 ? 0 : 3);
         sink.prepare(kba, kbb, G.va, G.vb);
-        const float2 er = mul2(dr, R.invR);
-        const float2 rho_r = fma2(er, er, sub2(one, er));
+        float2 rho_r = rho_prev;
+        if (!pc) {
+            const float2 er = mul2(dr, R.invR);
+            rho_r = fma2(er, er, sub2(one, er));
+        }
+        rho_prev = rho_r;
         float2 gr, gri;
         if constexpr (LUT) {
             const float2 ur = mul2(add2(R.u0, fma2(X0, R.aRx, fma2(X1, R.aRy, mul2(eta, R.aRz)))), rho_r);
@@ -1185,8 +1202,16 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
             amp_s = mul2(amp_s, make_float2(sqrtf(areaf.x), sqrtf(areaf.y)));
         }
         amps_prev = amp_s;
-        const float2 amp = LUT ? mul2(mul2(amp_s, ampt), mul2(R.ampr, rho_r))
-                               : mul2(mul2(mul2(amp_s, ampt), mul2(gr, R.ampr)), rho_r);
+        float2 amp;
+        if constexpr (LUT) {
+            amp = mul2(mul2(amp_s, ampt), mul2(R.ampr, rho_r));
+        } else {
+            // amp_s G_t G_r Rbar_t Rbar_r / (r_t r_r): everything but the channel's
+            // own Rbar_r / R_r is common to the phase centres of one antenna
+            const float2 ampc = pc ? ampc_prev : mul2(mul2(mul2(amp_s, ampt), gr), rho_r);
+            ampc_prev = ampc;
+            amp = mul2(ampc, R.ampr);
+        }
         const float2 vc = neg2(fma2(G.cu, qx, mul2(G.cv, qy)));
         float2 phi = fma2(dup(fi), Q.ax, Q.psi);
         phi = fma2(G.fj, Q.ay, phi);
