@@ -263,7 +263,8 @@ harm_status harm_batch_create(harm_scene *const *scenes, int32_t n_scenes, harm_
 
 /* Autotuner of the launch shape. Per scene-size class (fewer than 1e6 facets,
    fewer than 4e6, more) it times the persistent launch on the first 256 pulses
-   of the class's largest scene with each tile height (16 or 8 facet rows)
+   of the class's largest scenes (as many as give the launch at least eight waves
+   of work items) with each tile height (16 or 8 facet rows)
    and each time-Taylor window (harm_scene_info.pulse_batch pulses per work item,
    or half of it) -- 1 untimed and 3 timed launches per candidate, median -- and
    keeps the fastest, where a candidate replaces the default shape (16 rows, full

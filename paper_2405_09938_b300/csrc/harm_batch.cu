@@ -342,8 +342,10 @@ harm_status harm_batch_tune(harm_batch *b, void *const *iq)
     BCUDA(cudaEventCreate(&e0), "event");
     BCUDA(cudaEventCreate(&e1), "event");
     // the sample a candidate is timed on: the first kSamplePulses pulses of the
-    // (at most kSampleScenes) largest scenes of the class
-    const int kSamplePulses = 256, kSampleScenes = 1, kReps = 3;
+    // class's largest scenes, as many as give at least kSampleWaves waves of work
+    // items to the persistent launch (a sample that does not fill the GPU favours
+    // shapes with more, smaller items)
+    const int kSamplePulses = 256, kSampleWaves = 8, kReps = 3;
     // a candidate replaces the default shape (timed first) only when it is faster by
     // more than this margin: smaller differences on the sample are within its
     // run-to-run spread and do not carry over to the whole batch
@@ -357,7 +359,13 @@ harm_status harm_batch_tune(harm_batch *b, void *const *iq)
         if (members.empty()) continue;
         class_mask |= 1 << cls;
         std::vector<char> use(n, 0);
-        for (int i = 0; i < (int)members.size() && i < kSampleScenes; ++i) use[members[i]] = sample_all[members[i]] = 1;
+        long long items = 0;
+        const long long want = (long long)kSampleWaves * b->ctas_per_sm * b->sms;
+        for (int i = 0; i < (int)members.size() && items < want; ++i) {
+            const harm_scene *sc = b->scenes[members[i]];
+            use[members[i]] = sample_all[members[i]] = 1;
+            items += (long long)harm::batch_tiles(sc, 16) * ((kSamplePulses + sc->mixed.nb - 1) / sc->mixed.nb);
+        }
         const TuneKey key{b->device, b->variant, b->nc, b->taps, b->share3, cls};
         ClassChoice best{16, b->scenes[members[0]]->mixed.nb};
         auto it = g_class_choice.find(key);
