@@ -37,6 +37,7 @@
 // the epoch recurrence of Eq. 10). Each V is compiled in its own translation
 // unit, which includes this file and instantiates MixedLaunch<V>.
 #pragma once
+#include <cuda.h>  // CUtensorMap (type only: the library does not link the driver library)
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -1793,6 +1794,104 @@ __global__ void __launch_bounds__(NT, Var<V>::CWM ? 1 : 3)
     }
 }
 
+// Facet generator with tensor-memory-accelerator stores (three-field states,
+// nx % 4 == 0): the same contraction and Horner evaluation as
+// generate_mixed_kernel, but each pulse's [3][TY][TX] box of states is written to
+// shared memory and sent to the state array by one bulk tensor store, so the
+// threads issue no global stores and no 64-bit address arithmetic. Groups of
+// kGenGroup pulses rotate through three staging slots: before the barrier that
+// closes group g the issuing thread waits until the stores of group g - 2 have
+// read their slot, which group g + 1 reuses. The tensor map clips the box at the
+// scene's edges; the wave-table chunk of the contraction shares the staging
+// region (it is dead by then).
+constexpr int kGenGroup = 4;          // pulses per staging slot
+constexpr int kGenBox = 3 * TY * TX;  // floats of one pulse's box
+constexpr int kGenSlots = 3;
+
+// staging slots (128-byte aligned inside the region) and the window's pulse times
+__host__ __device__ constexpr int gen_tma_bytes()
+{
+    return 128 + kGenSlots * kGenGroup * kGenBox * 4 + NBG * 4 > wave_chunk_bytes(3)
+               ? 128 + kGenSlots * kGenGroup * kGenBox * 4 + NBG * 4
+               : wave_chunk_bytes(3);
+}
+
+// the threads' shared-memory writes become visible to the bulk copies
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, const float *src, int x, int y, int z, int w)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(src));
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(s), "r"(x), "r"(y), "r"(z), "r"(w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// every committed group but the newest has finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read_all_but_one()
+{
+    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+
+// every committed group is complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__global__ void __launch_bounds__(NT, 3)
+    generate_tma_kernel(const __grid_constant__ CUtensorMap map, MixedArgs A, int n0, int np, int b0)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const DevScene &S = A.S;
+    const Smem sm = carve(smem_raw, S.nc, false, 3);
+    const int tiles_x = (S.nx + TX - 1) / TX;
+    const int tx0 = (blockIdx.x % tiles_x) * TX;
+    const int ty0 = (blockIdx.x / tiles_x) * TY;
+    const int batch = b0 + blockIdx.y;
+    const int pa = max(n0, batch * A.nb);
+    const int pe = min(n0 + np, (batch + 1) * A.nb);
+    if (pa >= pe) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ix = tx0 + lane;
+    const int iya = ty0 + 2 * warp, iyb = iya + 1;
+    float2 C[3][kOrders];
+    item_coeffs<3, 4>(sm, A, batch, tx0, ty0, TY, ix, iya, iyb, C);
+    const unsigned raw_s = static_cast<unsigned>(__cvta_generic_to_shared(smem_raw));
+    float *slots = reinterpret_cast<float *>(smem_raw + ((128 - (raw_s & 127)) & 127));
+    float *tau_s = slots + kGenSlots * kGenGroup * kGenBox;
+    __syncthreads();  // the chunk region is dead
+    for (int i = threadIdx.x; i < pe - pa; i += NT) tau_s[i] = A.tau[pa + i];
+    __syncthreads();
+    const int at = 2 * warp * TX + lane;  // facet a in the box; facet b one row below
+    int slot = 0;
+    for (int n = pa; n < pe; n += kGenGroup) {
+        const int cnt = min(kGenGroup, pe - n);
+        float *bx = slots + slot * kGenGroup * kGenBox;
+#pragma unroll
+        for (int p = 0; p < kGenGroup; ++p) {
+            if (p < cnt) {
+                const float2 t = dup(tau_s[n - pa + p]);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float2 v = horner2(C[q], t);
+                    bx[p * kGenBox + q * TX * TY + at] = v.x;
+                    bx[p * kGenBox + q * TX * TY + at + TX] = v.y;
+                }
+            }
+        }
+        fence_async_shared();
+        if (threadIdx.x == 0) bulk_wait_read_all_but_one();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int p = 0; p < cnt; ++p) tma_store_4d(&map, bx + p * kGenBox, tx0, ty0, 0, n + p - n0);
+            bulk_commit();
+        }
+        slot = slot == kGenSlots - 1 ? 0 : slot + 1;
+    }
+    if (threadIdx.x == 0) bulk_wait_all();
+}
+
 MixedArgs make_args(const DevScene &S, const MixedTables &M)
 {
     MixedArgs A;
@@ -1946,6 +2045,19 @@ struct MixedLaunch {
                                 float *state)
     {
         const MixedArgs A = make_args(S, M);
+        if constexpr (Var<V>::NF == 3) {
+            alignas(64) CUtensorMap map;
+            if (np > 0 && M.nb <= NBG && S.nx % 4 == 0 && reinterpret_cast<uintptr_t>(state) % 16 == 0 &&
+                encode_state_map(&map, state, S.nx, S.ny, 3, np, TX, TY) == cudaSuccess) {
+                const int bytes = gen_tma_bytes();
+                cudaError_t e = prep(generate_tma_kernel, bytes);
+                if (e != cudaSuccess) return e;
+                return over_batches(S, M, TY, n0, np, [&](int bb, dim3 grid) {
+                    generate_tma_kernel<<<grid, NT, bytes, st>>>(map, A, n0, np, bb);
+                    return cudaGetLastError();
+                });
+            }
+        }
         // the kernel uses only the wave-table chunk: the rest of the SM's shared
         // memory stays L1 for the wave phasor tables it reads
         const int bytes = layout(S.nc, false, Var<V>::NF).w + wave_chunk_bytes(Var<V>::NF);

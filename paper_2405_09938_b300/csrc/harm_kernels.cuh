@@ -79,6 +79,13 @@ harm_status build_scene_tables(harm_scene *s);
 // holding it extends at least `bytes` past p (HARM_E_INVALID with a message
 // otherwise; NULL is invalid).
 harm_status check_device_span(const void *p, size_t bytes, const char *what);
+
+// Tensor map (CUtensorMap, 128 bytes at map) of a float32 state array
+// [np][nf][ny][nx] for bulk tensor stores of [nf][box_y][box_x] boxes, one pulse at
+// a time; needs nx % 4 == 0 and a 16-byte aligned state pointer. Fails (without
+// touching the device) when the driver offers no tensor-map encoder or rejects
+// the layout.
+cudaError_t encode_state_map(void *map, float *state, int nx, int ny, int nf, int np, int box_x, int box_y);
 void release_host_ring(harm_scene *s);  // copy stream, events and ring of harm_echo_accumulate_host
 harm_status build_mixed_tables(harm_scene *s, const std::vector<PulseState> &ps, const WaveSets &waves);
 // Separable phasor tables of every wave set, computed on the device in FP64 and

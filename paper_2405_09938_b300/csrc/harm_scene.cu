@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>  // CUtensorMap and its encoder's types (the encoder is fetched through the runtime)
+
 #include "harm.h"
 #include "harm_internal.cuh"
 #include "harm_kernels.cuh"
@@ -356,9 +358,46 @@ AddressRangeFn address_range_fn()
     return fn;
 }
 
+typedef int (*TensorMapEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tiled tensor-map encoder, fetched through the runtime; null when
+// the driver does not offer it.
+TensorMapEncodeFn tensor_map_encode_fn()
+{
+    static TensorMapEncodeFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<TensorMapEncodeFn>(f);
+    }();
+    return fn;
+}
+
 }  // namespace
 
 namespace harm {
+
+cudaError_t encode_state_map(void *map, float *state, int nx, int ny, int nf, int np, int box_x, int box_y)
+{
+    TensorMapEncodeFn fn = tensor_map_encode_fn();
+    if (!fn || nx <= 0 || ny <= 0 || np <= 0 || nx % 4 != 0 || reinterpret_cast<uintptr_t>(state) % 16 != 0)
+        return cudaErrorNotSupported;
+    const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nf, (cuuint64_t)np};
+    const cuuint64_t strides[3] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4, (cuuint64_t)nx * ny * nf * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)nf, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const int r = fn(static_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, state, dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == 0 ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 harm_status check_device_span(const void *p, size_t bytes, const char *what)
 {

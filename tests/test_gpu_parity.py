@@ -50,6 +50,34 @@ def test_generator_mixed_matches_oracle():
         assert err[1:].max() < 2e-6     # slopes
 
 
+def test_generator_mixed_many_items_per_cta():
+    """More work items (tiles x pulse windows) than twice the persistent grid of
+    the linear-surface generator: CTAs take three items in turn, so both
+    coefficient buffers are filled, released and refilled. Ragged tiles (300 x
+    170 facets) and a ragged first and last window (pulses 5 .. 1294)."""
+    import torch
+    from tests.gpu_util import take_pulses
+    d = small_wave_scene(n_pulses=1300, nx=300, ny=170)
+    n0, np_ = 5, 1290
+    scene = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
+    nb = harm.harm_scene_query(scene)["pulse_batch"]
+    tiles = -(-300 // 32) * -(-170 // 16)
+    windows = (n0 + np_ - 1) // nb - n0 // nb + 1
+    assert tiles * windows > 2 * 2 * torch.cuda.get_device_properties(0).multi_processor_count
+    st = torch.full((np_, 3, 170, 300), float("nan"), dtype=torch.float32, device="cuda")
+    harm.harm_facets_generate(scene, n0, np_, st)
+    harm.harm_scene_sync(scene)
+    pulses = [5, nb - 1, nb, 700, 1024, 1294]
+    got = take_pulses(st.reshape(np_, 1, -1).transpose(0, 1), [p - n0 for p in pulses])
+    scene.close()
+    assert not torch.isnan(st).any()
+    for i, n in enumerate(pulses):
+        want = oracle.facet_states(d, n).reshape(3, -1)
+        err = np.abs(got[0, i].reshape(3, -1).astype(np.float64) - want)
+        assert err[0].max() < 2e-6
+        assert err[1:].max() < 2e-6
+
+
 # ------------------------------------------------------------------ FP64 path
 @pytest.mark.parametrize("taps", [8, 1])
 def test_static_patch_fp64(taps):

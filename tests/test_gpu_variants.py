@@ -125,6 +125,28 @@ def test_cwm_generator_fields():
             assert np.abs(got[i] - want).max() < tol
 
 
+@pytest.mark.parametrize("nx", [152, 150])
+def test_hetero_generator_fields(nx):
+    """Three-field states of a heterogeneous sea (Eq. 1, 2) from the mixed
+    generator, every pulse of a window that starts and ends off the 256-pulse
+    time-Taylor windows. A width nx % 4 == 0 takes the generator whose states
+    leave shared memory by bulk tensor stores (clipped at the scene's edges),
+    other widths the one with direct stores."""
+    import torch
+    d = hs.hetero_sea(hs.ati_scene(n_pulses=300, nx=nx, ny=70, n_range=1024), tile_m=100.0)
+    n0, np_ = 17, 263
+    scene = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
+    st = torch.full((np_, 3, 70, nx), float("nan"), dtype=torch.float32, device="cuda")
+    harm.harm_facets_generate(scene, n0, np_, st)
+    harm.harm_scene_sync(scene)
+    got = st.cpu().numpy().astype(np.float64)
+    scene.close()
+    assert not np.isnan(got).any()
+    for n in (17, 18, 255, 256, 257, 279):
+        want = oracle.facet_states(d, n)
+        assert np.abs(got[n - n0] - want).max() < 6e-6
+
+
 def test_uv_grid_set_and_removed():
     import torch
     d = _base(n_pulses=48)
