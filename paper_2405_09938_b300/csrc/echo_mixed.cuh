@@ -793,8 +793,9 @@ __device__ __forceinline__ void warp_scatter_pair(const PairPlan &pl, float *buf
         for (int j = 0; j < 9; ++j) {
             const float a = sa ? (j > 0 ? ha[j - 1] : 0.0f) : (j < 8 ? ha[j] : 0.0f);
             const float b = sb ? (j > 0 ? hb[j - 1] : 0.0f) : (j < 8 ? hb[j] : 0.0f);
+            // (re, im) of the bin as one packed pair: b (srb, sib) + a (sra, sia)
             *reinterpret_cast<float2 *>(col[j & 3] + j * SROW) =
-                make_float2(fmaf(b, srb, a * sra), fmaf(b, sib, a * sia));
+                fma2(dup(b), make_float2(srb, sib), mul2(dup(a), make_float2(sra, sia)));
         }
     }
     __syncwarp();
