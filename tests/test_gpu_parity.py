@@ -78,6 +78,34 @@ def test_generator_mixed_many_items_per_cta():
         assert err[1:].max() < 2e-6
 
 
+@pytest.mark.parametrize("nx,ny,n0,np_", [(4, 3, 3, 1), (4, 3, 250, 9), (68, 21, 0, 37)])
+def test_generator_tensor_store_kernel_edges(nx, ny, n0, np_):
+    """The tensor-store generator (nx % 4 == 0) on a scene smaller than one tile,
+    a single pulse, a request that crosses a 256-pulse window, and ragged tiles;
+    then the same request into a state array that starts 4 bytes into its
+    allocation, which takes the direct-store kernel: the two kernels run the same
+    arithmetic, so their states agree bit for bit."""
+    import torch
+    d = small_wave_scene(n_pulses=300, nx=nx, ny=ny)
+    scene = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
+    n = np_ * 3 * ny * nx
+    st = torch.full((np_, 3, ny, nx), float("nan"), dtype=torch.float32, device="cuda")
+    harm.harm_facets_generate(scene, n0, np_, st)
+    flat = torch.full((n + 1,), float("nan"), dtype=torch.float32, device="cuda")
+    off = flat[1:]
+    assert off.data_ptr() % 16 == 4
+    harm.harm_facets_generate(scene, n0, np_, off)
+    harm.harm_scene_sync(scene)
+    got = st.cpu().numpy()
+    other = off.cpu().numpy().reshape(np_, 3, ny, nx)
+    scene.close()
+    assert not np.isnan(got).any()
+    assert np.array_equal(got.view(np.uint32), other.view(np.uint32))
+    for p in sorted({0, np_ // 2, np_ - 1}):
+        want = oracle.facet_states(d, n0 + p)
+        assert np.abs(got[p].astype(np.float64) - want).max() < 2e-6
+
+
 # ------------------------------------------------------------------ FP64 path
 @pytest.mark.parametrize("taps", [8, 1])
 def test_static_patch_fp64(taps):
