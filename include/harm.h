@@ -186,8 +186,13 @@ harm_status harm_scene_set_pattern(harm_scene *scene, int32_t antenna, int32_t n
    scenes and in float for HARM_PREC_MIXED and HARM_PREC_FP32 scenes. F = 3 fields (eta, eta_x,
    eta_y) for the linear surface; F = 8 with the Choppy Wave Model: (eta, eta_x,
    eta_y, D_x, D_y, dD_x/dx, dD_x/dy, dD_y/dy), D the horizontal displacement and
-   every derivative taken with respect to the rest position.
-   Errors: HARM_E_INVALID for an out-of-range pulse window or NULL pointer. */
+   every derivative taken with respect to the rest position. For mixed scenes with
+   F = 3, nx % 4 == 0 and a 16-byte aligned state_dev the states leave the GPU's
+   shared memory by bulk tensor stores (one [3][16][32] box per tile and pulse); any
+   other layout takes direct stores. Both write the same bits. state_dev is owned by
+   the caller and must hold np * F * n_facets elements of device memory.
+   Errors: HARM_E_INVALID for an out-of-range pulse window, a NULL, host or too-short
+   pointer; HARM_E_CUDA for a launch failure. */
 harm_status harm_facets_generate(harm_scene *scene, int32_t n0, int32_t np, void *state_dev);
 
 /* Echo accumulator (Eq. 3, 4, 16, 17): adds the echo of every facet for pulses
