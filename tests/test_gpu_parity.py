@@ -106,6 +106,20 @@ def test_generator_tensor_store_kernel_edges(nx, ny, n0, np_):
         assert np.abs(got[p].astype(np.float64) - want).max() < 2e-6
 
 
+def test_generator_static_surface_is_flat():
+    """A static surface (100 x 100 facets, nx % 4 == 0: the tensor-store kernel)
+    has zero height and slopes at every pulse: every state written, every one 0."""
+    import torch
+    d = hs.small_static()
+    scene = harm.harm_scene_create(d, harm.HARM_PREC_MIXED)
+    st = torch.full((7, 3, d["ny"], d["nx"]), float("nan"), dtype=torch.float32, device="cuda")
+    harm.harm_facets_generate(scene, 20, 7, st)
+    harm.harm_scene_sync(scene)
+    got = st.cpu().numpy()
+    scene.close()
+    assert np.array_equal(got, np.zeros_like(got))
+
+
 # ------------------------------------------------------------------ FP64 path
 @pytest.mark.parametrize("taps", [8, 1])
 def test_static_patch_fp64(taps):
