@@ -60,7 +60,7 @@ constexpr int WA = 32;        // range bins per channel of the adjoint's residua
 constexpr int WA_LO = 14;     // (a 32 x 16 facet tile spans about +-10 bins around its
                               // reference bin, taps and heights included; residuals
                               // outside the window are read from global memory)
-constexpr int NBR = 16;       // pulses per chunk of FP64 tile references
+constexpr int NBR = 32;       // pulses per chunk of FP64 tile references
 constexpr int NBG = 256;      // pulses per work item (time-Taylor window of the generator;
                               // |omega tau| <= 0.2 on the headline wave spectrum)
 constexpr int WCH = 64;       // wave components per shared-memory chunk of the generator
@@ -109,9 +109,11 @@ struct __align__(16) PulseRec {
     int pad;
 };
 
-// The same references with every value duplicated into a pair (v, v): the
-// forward path evaluates two facets per thread with packed FP32x2 arithmetic and
-// reads each reference as one 64-bit operand.
+// The same references with every value duplicated into a pair (v, v), formed in
+// registers where a packed two-facet step reads a record (dup_rec, dup_chan):
+// the packed FP32x2 arithmetic takes each reference as one 64-bit operand, while
+// shared memory holds only the scalar records (half the bytes and loads of a
+// duplicated layout, which leaves room for 32-pulse reference chunks).
 struct __align__(16) AntRec2 {
     float2 ux, uy, uz, invR;
     float2 inv2R, inv2R2, u0, v0;
@@ -179,7 +181,7 @@ struct Layout {
 // Every region starts on a 16-byte boundary (regions are read with 128-bit loads).
 __host__ __device__ inline int align16(int o) { return (o + 15) & ~15; }
 
-__host__ __device__ inline Layout layout(int nc, bool dup, int nf)
+__host__ __device__ inline Layout layout(int nc, int nf)
 {
     Layout L;
     int o = 0;
@@ -189,14 +191,15 @@ __host__ __device__ inline Layout layout(int nc, bool dup, int nf)
     L.stage = o;
     o += wbytes > sbytes ? wbytes : sbytes;
     L.tile = o = align16(o);  o += kTileBufs * nc * WT * 8;
-    L.tx = o = align16(o);    o += NBR * (int)(dup ? sizeof(AntRec2) : sizeof(AntRec));
-    L.rx = o = align16(o);    o += NBR * nc * (int)(dup ? sizeof(AntRec2) : sizeof(AntRec));
-    L.ch = o = align16(o);    o += NBR * nc * (int)(dup ? sizeof(ChanRec2) : sizeof(ChanRec));
+    L.tx = o = align16(o);    o += NBR * (int)sizeof(AntRec);
+    L.rx = o = align16(o);    o += NBR * nc * (int)sizeof(AntRec);
+    L.ch = o = align16(o);    o += NBR * nc * (int)sizeof(ChanRec);
     L.pr = o = align16(o);    o += NBR * (int)sizeof(PulseRec);
     L.txd = o = align16(o);   o += NBR * 4 * 8;
     L.lut = o = align16(o);   o += (1 + kMaxCh) * (int)sizeof(PatLutF);
-    // Taylor coefficients of the thread's two facets, [3][kOrders][NT] float2, for the
-    // linear surface (the 8-field CWM keeps them in registers)
+    // Taylor coefficients of the thread's two facets, [3][kOrders / 2][NT] float4 (the
+    // pairs of orders 2q and 2q + 1), for the linear surface (the 8-field CWM keeps
+    // them in registers)
     L.coef = o = align16(o);  o += nf == 3 ? 3 * kOrders * NT * 8 : 0;
     L.total = align16(o);
     return L;
@@ -207,22 +210,19 @@ struct Smem {
     float2 *wx;      // [WCH][TX] e^{i kx x} of the tile's columns
     float2 *wy;      // [WCH][TY] a e^{i (ky y + phi)} of the tile's rows
     float2 *tile;    // [kTileBufs][nc][WT]
-    AntRec *tx;      // [NBR]          (scalar layout: adjoint)
+    AntRec *tx;      // [NBR]
     AntRec *rx;      // [NBR][nc]
     ChanRec *ch;     // [NBR][nc]
-    AntRec2 *tx2;    // [NBR]          (pair layout: forward, same memory)
-    AntRec2 *rx2;    // [NBR][nc]
-    ChanRec2 *ch2;   // [NBR][nc]
     PulseRec *pr;    // [NBR]
     double *txd;     // [NBR][4]
     float *stage;    // [NWARP][SBINS][SROW]
     PatLutF *lut;    // [1 + nc] u-v gain grids (LUT variant)
-    float2 *coef;    // [3][kOrders][NT] Taylor coefficients (linear surface)
+    float2 *coef;    // [3][kOrders / 2][NT] float4 Taylor coefficients (linear surface)
 };
 
-__device__ __forceinline__ Smem carve(unsigned char *raw, int nc, bool dup, int nf)
+__device__ __forceinline__ Smem carve(unsigned char *raw, int nc, int nf)
 {
-    Layout L = layout(nc, dup, nf);
+    Layout L = layout(nc, nf);
     Smem s;
     s.w = reinterpret_cast<float2 *>(raw + L.w);
     s.wx = reinterpret_cast<float2 *>(raw + L.w + WCH * nf * kOrders * 4);
@@ -231,9 +231,6 @@ __device__ __forceinline__ Smem carve(unsigned char *raw, int nc, bool dup, int 
     s.tx = reinterpret_cast<AntRec *>(raw + L.tx);
     s.rx = reinterpret_cast<AntRec *>(raw + L.rx);
     s.ch = reinterpret_cast<ChanRec *>(raw + L.ch);
-    s.tx2 = reinterpret_cast<AntRec2 *>(raw + L.tx);
-    s.rx2 = reinterpret_cast<AntRec2 *>(raw + L.rx);
-    s.ch2 = reinterpret_cast<ChanRec2 *>(raw + L.ch);
     s.pr = reinterpret_cast<PulseRec *>(raw + L.pr);
     s.txd = reinterpret_cast<double *>(raw + L.txd);
     s.stage = reinterpret_cast<float *>(raw + L.stage);
@@ -337,6 +334,7 @@ __device__ void tile_ref(const AntState &A, double xr, double yr, double u[3], d
 
 __device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
 
+// The pair forms of a record at its use (see AntRec2).
 __device__ __forceinline__ AntRec2 dup_rec(const AntRec &r)
 {
     AntRec2 o;
@@ -347,9 +345,16 @@ __device__ __forceinline__ AntRec2 dup_rec(const AntRec &r)
     return o;
 }
 
+__device__ __forceinline__ ChanRec2 dup_chan(const ChanRec &q)
+{
+    ChanRec2 o;
+    o.psi = dup(q.psi); o.ax = dup(q.ax); o.ay = dup(q.ay); o.gam = dup(q.gam); o.pfrac = dup(q.pfrac);
+    o.kbase = q.kbase; o.gx = q.gx; o.gy = q.gy; o.pad0 = 0;
+    return o;
+}
+
 // Transmit references of pulse pa + t: record, FP64 unit vector and range offset,
 // pulse record.
-template <bool DUP>
 __device__ __forceinline__ void tx_refs(const Smem &sm, const MixedArgs &A, int pa, int t, double xr, double yr)
 {
     const DevScene &S = A.S;
@@ -358,10 +363,7 @@ __device__ __forceinline__ void tx_refs(const Smem &sm, const MixedArgs &A, int 
     double u[3], dref;
     AntRec r;
     tile_ref(P.tx, xr, yr, u, dref, r);
-    if (DUP)
-        sm.tx2[t] = dup_rec(r);
-    else
-        sm.tx[t] = r;
+    sm.tx[t] = r;
     sm.txd[4 * t + 0] = u[0];
     sm.txd[4 * t + 1] = u[1];
     sm.txd[4 * t + 2] = u[2];
@@ -376,7 +378,6 @@ __device__ __forceinline__ void tx_refs(const Smem &sm, const MixedArgs &A, int 
 
 // Channel record t = (pulse pi, channel c) from the receive references (u, dref,
 // r) and the pulse's transmit references in shared memory.
-template <bool DUP>
 __device__ __forceinline__ void rx_combine(const Smem &sm, const MixedArgs &A, int pa, int t, const double u[3],
                                            double dref, const AntRec &r)
 {
@@ -403,23 +404,8 @@ __device__ __forceinline__ void rx_combine(const Smem &sm, const MixedArgs &A, i
     double kb = floor(p);
     q.kbase = (int)kb;
     q.pfrac = (float)(p - kb);
-    if (DUP) {
-        sm.rx2[t] = dup_rec(r);
-        ChanRec2 q2;
-        q2.psi = dup(q.psi);
-        q2.ax = dup(q.ax);
-        q2.ay = dup(q.ay);
-        q2.gam = dup(q.gam);
-        q2.pfrac = dup(q.pfrac);
-        q2.kbase = q.kbase;
-        q2.gx = q.gx;
-        q2.gy = q.gy;
-        q2.pad0 = 0;
-        sm.ch2[t] = q2;
-    } else {
-        sm.rx[t] = r;
-        sm.ch[t] = q;
-    }
+    sm.rx[t] = r;
+    sm.ch[t] = q;
 }
 
 // FP64 references of the batch's pulses [pa, pe) for the tile reference point
@@ -428,9 +414,8 @@ __device__ __forceinline__ void rx_combine(const Smem &sm, const MixedArgs &A, i
 // warp-aligned threads) are formed at the same time and the channel records
 // combine them after one barrier (the adjoint: 1.4 % faster); otherwise, and when
 // the CTA has too few threads for that, the transmit stage runs first (the
-// forward, whose pulse loop keeps more registers live across the call). DUP
-// selects the pair layout of the packed path.
-template <bool DUP, bool CONCURRENT>
+// forward, whose pulse loop keeps more registers live across the call).
+template <bool CONCURRENT>
 __device__ void build_refs(const Smem &sm, const MixedArgs &A, int pa, int pe, double xr, double yr)
 {
     const DevScene &S = A.S;
@@ -445,20 +430,20 @@ __device__ void build_refs(const Smem &sm, const MixedArgs &A, int pa, int pe, d
             const RxState &Rs = S.rx[(size_t)(pa + t / S.nc) * S.nc + t % S.nc];
             tile_ref(Rs.rx, xr, yr, u, dref, r);
         } else if (t >= txb && t < txb + npb) {
-            tx_refs<DUP>(sm, A, pa, t - txb, xr, yr);
+            tx_refs(sm, A, pa, t - txb, xr, yr);
         }
         __syncthreads();
-        if (t < nrx) rx_combine<DUP>(sm, A, pa, t, u, dref, r);
+        if (t < nrx) rx_combine(sm, A, pa, t, u, dref, r);
         return;
     }
-    for (int t = threadIdx.x; t < npb; t += NT) tx_refs<DUP>(sm, A, pa, t, xr, yr);
+    for (int t = threadIdx.x; t < npb; t += NT) tx_refs(sm, A, pa, t, xr, yr);
     __syncthreads();
     for (int t = threadIdx.x; t < nrx; t += NT) {
         const RxState &Rs = S.rx[(size_t)(pa + t / S.nc) * S.nc + t % S.nc];
         double u[3], dref;
         AntRec r;
         tile_ref(Rs.rx, xr, yr, u, dref, r);
-        rx_combine<DUP>(sm, A, pa, t, u, dref, r);
+        rx_combine(sm, A, pa, t, u, dref, r);
     }
 }
 
@@ -1103,7 +1088,7 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
     const float2 inv_n = make_float2(rsqrtf(nn.x), rsqrtf(nn.y));
 
     // transmit leg (shared by the channels)
-    const AntRec2 T = sm.tx2[pi];
+    const AntRec2 T = dup_rec(sm.tx[pi]);
     const float2 at = fma2(T.ux, X0, fma2(T.uy, X1, mul2(T.uz, eta)));
     const float2 st = fma2(neg2(at), at, b2);
     const float2 qt = mul2(st, fma2(neg2(at), T.inv2R2, T.inv2R));
@@ -1123,8 +1108,8 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
     // with u-v grids the transmit gain stays out of the real amplitude
     const float2 ampt = LUT ? mul2(T.ampr, rho_t) : mul2(mul2(gt, T.ampr), rho_t);
 
-    const AntRec2 *RX = sm.rx2 + pi * nc;
-    const ChanRec2 *CH = sm.ch2 + pi * nc;
+    const AntRec *RX = sm.rx + pi * nc;
+    const ChanRec *CH = sm.ch + pi * nc;
     float2 gr_prev = make_float2(0.0f, 0.0f), amps_prev = make_float2(0.0f, 0.0f);
     // with the six-channel layout known at compile time, channels 1, 2 and 4, 5 are
     // the second and third phase centres of the antenna of channels 0 and 3 (5 m
@@ -1137,8 +1122,8 @@ __device__ __forceinline__ void facet_pulse2(const Smem &sm, const MixedArgs &A,
 #pragma unroll CU
     for (int ch = 0; ch < nc; ++ch) {
         const bool pc = SH3 && (ch % 3 != 0);  // a later phase centre of the antenna (compile time)
-        const AntRec2 R = RX[ch];
-        const ChanRec2 Q = CH[ch];
+        const AntRec2 R = dup_rec(RX[ch]);
+        const ChanRec2 Q = dup_chan(CH[ch]);
         const float2 ar = fma2(R.ux, X0, fma2(R.uy, X1, mul2(R.uz, eta)));
         float2 qr = qr_prev;
         if (!pc) {
@@ -1368,7 +1353,8 @@ __device__ __forceinline__ void item_coeffs(const Smem &sm, const MixedArgs &A, 
 
 // Keep the item's Taylor coefficients where the pulse loop reads them: a
 // thread-private column of shared memory for the linear surface (frees 36
-// registers for the per-channel arithmetic), registers for the CWM.
+// registers for the per-channel arithmetic; two orders per 128-bit load),
+// registers for the CWM.
 template <int NF>
 __device__ __forceinline__ void store_coeffs(const Smem &sm, const float2 C[NF][kOrders])
 {
@@ -1376,7 +1362,9 @@ __device__ __forceinline__ void store_coeffs(const Smem &sm, const float2 C[NF][
 #pragma unroll
         for (int f = 0; f < NF; ++f)
 #pragma unroll
-            for (int o = 0; o < kOrders; ++o) sm.coef[(f * kOrders + o) * NT + threadIdx.x] = C[f][o];
+            for (int q = 0; q < kOrders / 2; ++q)
+                reinterpret_cast<float4 *>(sm.coef)[(f * (kOrders / 2) + q) * NT + threadIdx.x] =
+                    make_float4(C[f][2 * q].x, C[f][2 * q].y, C[f][2 * q + 1].x, C[f][2 * q + 1].y);
     }
 }
 
@@ -1386,13 +1374,17 @@ __device__ __forceinline__ void eval_state(const Smem &sm, const float2 C[NF][kO
 {
     const float2 t = dup(tau);
     if constexpr (NF == 3) {
-        const float2 *cs = sm.coef + threadIdx.x;
+        const float4 *cs = reinterpret_cast<const float4 *>(sm.coef) + threadIdx.x;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
-            float2 r = cs[(f * kOrders + kOrders - 1) * NT];
+            float2 c[kOrders];
 #pragma unroll
-            for (int o = kOrders - 2; o >= 0; --o) r = fma2(r, t, cs[(f * kOrders + o) * NT]);
-            st[f] = r;
+            for (int q = 0; q < kOrders / 2; ++q) {
+                const float4 v = cs[(f * (kOrders / 2) + q) * NT];
+                c[2 * q] = make_float2(v.x, v.y);
+                c[2 * q + 1] = make_float2(v.z, v.w);
+            }
+            st[f] = horner2(c, t);
         }
     } else {
 #pragma unroll
@@ -1463,7 +1455,7 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
     for (int c0 = I.pa; c0 < I.pe; c0 += NBR) {
         const int ce = min(c0 + NBR, I.pe);
         __syncthreads();  // the previous chunk's flush is done with the records
-        build_refs<true, false>(sm, A, c0, ce, xr, yr);
+        build_refs<false>(sm, A, c0, ce, xr, yr);
         __syncthreads();
         for (int n = c0; n < ce;) {
             // speckle of the epoch of pulse n, then the chunk's pulses of that epoch
@@ -1501,7 +1493,7 @@ __device__ void forward_item(const Smem &sm, const MixedArgs &A, const PolyArgs 
                             float2 *slot = sm.tile + (pb * nc + ch) * WT + w;
                             float2 v = *slot;
                             *slot = make_float2(0.f, 0.f);
-                            int k = sm.ch2[pp * nc + ch].kbase - WT_LO + w;
+                            int k = sm.ch[pp * nc + ch].kbase - WT_LO + w;
                             if ((v.x != 0.0f || v.y != 0.0f) && k >= 0 && k < S.nr)
                                 gadd<OutT>(iq + 2 * ((size_t)ch * np + (p - n0)) * S.nr, (size_t)k, v.x, v.y);
                         }
@@ -1526,7 +1518,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     accumulate_mixed_kernel(MixedArgs A, PolyArgs P, int n0, int np, int b0, int ty, OutT *iq)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Smem sm = carve(smem_raw, A.S.nc, true, Var<V>::NF);
+    const Smem sm = carve(smem_raw, A.S.nc, Var<V>::NF);
     const ItemGeo I = item_geo(A, blockIdx.x, b0 + blockIdx.y, ty, n0, np);
     if (I.pa >= I.pe) return;
     clear_smem(sm, A.S.nc);
@@ -1540,7 +1532,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     probe_mixed_kernel(MixedArgs A, PolyArgs P, int n0, int np, int b0, ProbeOut out)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Smem sm = carve(smem_raw, A.S.nc, true, Var<V>::NF);
+    const Smem sm = carve(smem_raw, A.S.nc, Var<V>::NF);
     const ItemGeo I = item_geo(A, blockIdx.x, b0 + blockIdx.y, TY, n0, np);
     if (I.pa >= I.pe) return;
     clear_smem(sm, A.S.nc);
@@ -1572,7 +1564,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     __shared__ MixedArgs args;
     __shared__ int s_item, s_scene;
     const int nc_max = B.args[0].S.nc;  // layout sized for the first scene's channels (all equal)
-    const Smem sm = carve(smem_raw, nc_max, true, Var<V>::NF);
+    const Smem sm = carve(smem_raw, nc_max, Var<V>::NF);
     int cur_scene = -1;
     clear_smem(sm, nc_max);
     for (;;) {
@@ -1658,7 +1650,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DevScene &S = A.S;
     const int nc = S.nc;
-    const Smem sm = carve(smem_raw, nc, true, NF);
+    const Smem sm = carve(smem_raw, nc, NF);
     const int tiles_x = (S.nx + TX - 1) / TX;
     const int tx0 = (blockIdx.x % tiles_x) * TX;
     const int ty0 = (blockIdx.x / tiles_x) * TY;
@@ -1703,7 +1695,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
     for (int c0 = pa; c0 < pe; c0 += NBR) {
         const int ce = min(c0 + NBR, pe);
         __syncthreads();  // the previous chunk is done with the records
-        build_refs<true, true>(sm, A, c0, ce, xr, yr);
+        build_refs<true>(sm, A, c0, ce, xr, yr);
         for (int n = c0; n < ce;) {
             __syncthreads();
             // speckle of the epoch of pulse n, then the chunk's pulses of that epoch
@@ -1725,7 +1717,7 @@ __global__ void __launch_bounds__(NT, Var<V>::MIN_BLOCKS)
                 // residual window of this pulse, every channel
                 for (int i = threadIdx.x; i < nc * WA; i += NT) {
                     int ch = i / WA, w = i % WA;
-                    int k = sm.ch2[pi * nc + ch].kbase - WA_LO + w;
+                    int k = sm.ch[pi * nc + ch].kbase - WA_LO + w;
                     float2 v = make_float2(0.f, 0.f);
                     if (k >= 0 && k < S.nr) {
                         const InT *r = resid + 2 * (((size_t)ch * np + (n - n0)) * S.nr + k);
@@ -1754,7 +1746,7 @@ __global__ void __launch_bounds__(NT, Var<V>::CWM ? 1 : 3)
     constexpr int NF = Var<V>::NF;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DevScene &S = A.S;
-    const Smem sm = carve(smem_raw, S.nc, false, NF);
+    const Smem sm = carve(smem_raw, S.nc, NF);
     const int tiles_x = (S.nx + TX - 1) / TX;
     const int tx0 = (blockIdx.x % tiles_x) * TX;
     const int ty0 = (blockIdx.x / tiles_x) * TY;
@@ -1845,7 +1837,7 @@ __global__ void __launch_bounds__(NT, 3)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const DevScene &S = A.S;
-    const Smem sm = carve(smem_raw, S.nc, false, 3);
+    const Smem sm = carve(smem_raw, S.nc, 3);
     const int tiles_x = (S.nx + TX - 1) / TX;
     const int tx0 = (blockIdx.x % tiles_x) * TX;
     const int ty0 = (blockIdx.x / tiles_x) * TY;
@@ -1963,7 +1955,7 @@ cudaError_t accumulate_nc(const DevScene &S, const MixedTables &M, cudaStream_t 
 {
     const MixedArgs A = make_args(S, M);
     const PolyArgs P = make_poly(M);
-    const int bytes = layout(S.nc, true, Var<V>::NF).total;
+    const int bytes = layout(S.nc, Var<V>::NF).total;
     cudaError_t e = prep(accumulate_mixed_kernel<TAPS, OutT, V, NCC, SH3>, bytes);
     if (e != cudaSuccess) return e;
     return over_batches(S, M, TY, n0, np, [&](int bb, dim3 grid) {
@@ -1990,7 +1982,7 @@ cudaError_t probe_nc(const DevScene &S, const MixedTables &M, cudaStream_t st, i
 {
     const MixedArgs A = make_args(S, M);
     const PolyArgs P = make_poly(M);
-    const int bytes = layout(S.nc, true, Var<V>::NF).total;
+    const int bytes = layout(S.nc, Var<V>::NF).total;
     cudaError_t e = prep(probe_mixed_kernel<TAPS, V, NCC, SH3>, bytes);
     if (e != cudaSuccess) return e;
     return over_batches(S, M, TY, n0, np, [&](int bb, dim3 grid) {
@@ -2017,7 +2009,7 @@ cudaError_t adjoint_nc(const DevScene &S, const MixedTables &M, cudaStream_t st,
 {
     const MixedArgs A = make_args(S, M);
     const PolyArgs P = make_poly(M);
-    const int bytes = layout(S.nc, true, Var<V>::NF).total;
+    const int bytes = layout(S.nc, Var<V>::NF).total;
     cudaError_t e = prep(adjoint_mixed_kernel<TAPS, InT, V, NCC, SH3>, bytes);
     if (e != cudaSuccess) return e;
     return over_batches(S, M, TY, n0, np, [&](int bb, dim3 grid) {
@@ -2061,7 +2053,7 @@ struct MixedLaunch {
         }
         // the kernel uses only the wave-table chunk: the rest of the SM's shared
         // memory stays L1 for the wave phasor tables it reads
-        const int bytes = layout(S.nc, false, Var<V>::NF).w + wave_chunk_bytes(Var<V>::NF);
+        const int bytes = layout(S.nc, Var<V>::NF).w + wave_chunk_bytes(Var<V>::NF);
         cudaError_t e = prep(generate_mixed_kernel<V>, bytes);
         if (e != cudaSuccess) return e;
         return over_batches(S, M, TY, n0, np, [&](int bb, dim3 grid) {
@@ -2108,7 +2100,7 @@ struct MixedLaunch {
         B.n = L.n;
         B.total = L.total;
         const PolyArgs P = make_poly(*L.poly);
-        const int bytes = layout(L.nc, true, Var<V>::NF).total;
+        const int bytes = layout(L.nc, Var<V>::NF).total;
         cudaError_t e;
         if (L.taps == 1) {
             if ((e = prep(batch_mixed_kernel<1, V, 0>, bytes)) != cudaSuccess) return e;
