@@ -138,12 +138,12 @@ ALGO_FLOPS_ACCUMULATOR = 150.0
 ALGO_FLOPS_GENERATOR_PER_FACET_PULSE = 3072.0
 # What the kernel executes per contribution, from the instruction-mix counters on
 # the 512-pulse capture of the headline scene (FFMA2 = 4 flops, FFMA / FMUL2 /
-# FADD2 = 2, FMUL / FADD = 1; per contribution 40.33 FFMA2 + 0.50 FFMA + 13.79 FMUL2
+# FADD2 = 2, FMUL / FADD = 1; per contribution 40.33 FFMA2 + 0.50 FFMA + 13.88 FMUL2
 # + 2.43 FMUL + 8.55 FADD2 + 1.48 FADD): the time-Taylor generator replaces the
 # direct synthesis, so this is far below the algorithmic count.
-EXECUTED_FLOPS_PER_CONTRIBUTION = 210.9
+EXECUTED_FLOPS_PER_CONTRIBUTION = 211.1
 # All instructions issued per contribution (thread level, same capture).
-INSTR_PER_CONTRIBUTION = 179.9
+INSTR_PER_CONTRIBUTION = 175.7
 # DRAM bytes (read + write) of one headline launch (2048 pulses), from one ncu
 # capture of dram__bytes_read.sum + dram__bytes_write.sum, and the SHA-256 of the
 # kernel sources' code (comments and blank lines dropped) it was taken on: the
